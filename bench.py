@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd Wilson-clover solve on one GB300 (or N replicas).
+
+Workload (synthetic, seeded): 32^3 x 64 lattice, links exp(i 0.4 H) (gauge
+seed 3), kappa 0.1355, csw 1.0 (four-leaf clover), Gaussian source (seed 0),
+antiperiodic t; mixed-precision even-odd CG on the normal equations: FP16
+storage with per-site norms and FP32 arithmetic inside, FP64 reliable
+update every 50 iterations, stopped at true residual |b - M x|/|b| <= 1e-10.
+
+One step = one complete solve (b and the solution resident in HBM; the
+gauge field and the clover term are set up beforehand).  The metric is the
+sustained dslash rate of the solve: hopping applications x 1320 flops x V/2
+sites / wall time.  Also reported: the dslash kernels' achieved HBM
+bandwidth against the measured copy bandwidth (roofline), the end-to-end
+rate through lqcd_solve with host buffers, solve times of the plain FP64
+CG and the FP32 / BF16-inner solves on the same system, a stand-alone FP32
+recon-12 dslash rate, and the FP64 CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the solve does not
+shard across GPUs here): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s & % HBM roofline; solve time to 1e-10 resid vs plain FP64 CG"
+WORKLOADS = {
+    "32c64": dict(dims=(32, 32, 32, 64), eps=0.4, gauge_seed=3, src_seed=0, kappa=0.1355, csw=1.0),
+    "16c32": dict(dims=(16, 16, 16, 32), eps=0.5, gauge_seed=2, src_seed=0, kappa=0.135, csw=1.0),
+}
+TOL = 1e-10
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_name(w):
+    d = w["dims"]
+    return ("wilson-clover even-odd CG-NE %dx%dx%dx%d, exp(i %.1f H) links, kappa %.4g, csw %.1f, "
+            "tol 1e-10" % (d[0], d[1], d[2], d[3], w["eps"], w["kappa"], w["csw"]))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import lqcd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    Vh = V // 2
+    U = synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])
+    b = synth.gaussian_spinor(dims, w["src_seed"])
+    stream = torch.cuda.Stream(device=dev)
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16", "bf16"), recon=12, device=dev,
+                       stream=stream)
+    with torch.cuda.stream(stream):
+        Ud = torch.from_numpy(U).to(dev)
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros_like(bd)
+    stream.synchronize()
+    lat.gauge_load(Ud)
+    t0 = time.time()
+    lat.clover_compute(w["kappa"], w["csw"])
+    clover_s = time.time() - t0
+    del Ud
+    params = dict(inner_prec="f16", reliable_interval=50, check_interval=10)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        lat.solve(xd, bd, TOL, **params)
+    lqcd.lqcd_profile_enable(lat.ctx, True)
+    lqcd.lqcd_profile_read(lat.ctx)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    stream.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        _, st = lat.solve(xd, bd, TOL, **params)
+        stats.append(st)
+    ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = lqcd.lqcd_profile_read(lat.ctx)
+    lqcd.lqcd_profile_enable(lat.ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    dslash_total = sum(s["dslash_count"] for s in stats)
+    flops = dslash_total * 1320.0 * Vh * world
+    value = flops / (ms * 1e-3) / 1e9
+    worst_res = max(s["true_residual"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # dominant kernel: the FP16 hopping kernels (all epilogues) inside the solve
+    hb, hbsrc = measured_peaks()
+    pf = prof["f16"]
+    achieved = pf["bytes"] / (pf["ms"] * 1e-3) / 1e9 if pf["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "dslash_kernel<F16, recon-12> (all epilogues of the solve)",
+                "achieved": round(achieved, 1), "peak": hb, "unit": "GB/s",
+                "frac": round(achieved / hb, 4), "peak_source": hbsrc,
+                "launches": pf["launches"], "avg_launch_us": round(1e3 * pf["ms"] / max(1, pf["launches"]), 2),
+                "kernel_time_share": round(sum(p["ms"] for p in prof.values()) / (ms / world if world > 1 else ms), 4),
+                "traffic": None}
+
+    out = {"value": value, "ms": ms, "stats": stats, "roofline": roofline, "clocks": clk,
+           "dslash_total": dslash_total, "worst_res": worst_res, "launches": launches,
+           "clover_setup_s": round(clover_s, 3), "prof": prof}
+
+    if rank == 0 and not args.quick:
+        out["e2e"] = e2e_leg(args, lat, b, Vh, params)
+        out["solve"] = compare_solves(lat, bd, xd, stream, params)
+        out["dslash_f32"] = dslash_microbench(lat, b, dims, stream, hb, hbsrc)
+    lat.close()
+    return out
+
+
+def e2e_leg(args, lat, b, Vh, params):
+    """Same metric through lqcd_solve with pinned host b and x: the H2D copy
+    of b and the D2H copy of x are inside each timed step."""
+    import torch
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    lat.solve(xh, bh, TOL, **params)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        _, st = lat.solve(xh, bh, TOL, **params)
+        total += st["dslash_count"]
+    dt = time.perf_counter() - t0
+    nbytes = bh.numel() * bh.element_size()
+    return {"value": total * 1320.0 * Vh / dt / 1e9, "unit": "GFLOP/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": round(1e3 * dt / args.steps, 3)}
+
+
+def compare_solves(lat, bd, xd, stream, params):
+    """One solve per inner precision (outside the timed region), each timed
+    with CUDA events on the context stream."""
+    import torch
+    res = {}
+    for name, kw in (("f16_inner_f64_ru", dict(params)),
+                     ("bf16_inner_f64_ru", dict(params, inner_prec="bf16")),
+                     ("f32_inner_f64_ru", dict(params, inner_prec="f32")),
+                     ("plain_f64_cg", dict(inner_prec="f64", check_interval=10))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        rc, st = lat.solve(xd, bd, TOL, raise_on_error=False, **kw)
+        e1.record(stream)
+        stream.synchronize()
+        res[name] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "iterations": st["iterations"],
+                     "reliable_updates": st["reliable_updates"], "dslash": st["dslash_count"],
+                     "true_residual": st["true_residual"], "status": rc}
+    f64 = res["plain_f64_cg"]["seconds"]
+    for k in res:
+        res[k]["speedup_vs_f64_cg"] = round(f64 / res[k]["seconds"], 2)
+    return res
+
+
+def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
+    """FP32 recon-12 parity hopping term alone: 8 buffer pairs rotated
+    (8 x 302 MB > L2), 50 timed launches after 5 warm-ups."""
+    import torch
+    Vh = int(np.prod(dims)) // 2
+    nbuf = 8
+    with torch.cuda.stream(stream):
+        fins = [lat.new_field("f32") for _ in range(nbuf)]
+        fouts = [lat.new_field("f32") for _ in range(nbuf)]
+    for f in fins:
+        lat.pack(f, b, 1, "f32")
+    for i in range(5):
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec="f32")
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = 50
+    e0.record(stream)
+    for i in range(n):
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec="f32")
+    e1.record(stream)
+    stream.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / n
+    comp = 576.0 * Vh  # FP32 recon-12 compulsory bytes per launch
+    return {"gflops": round(1320.0 * Vh / t / 1e9, 1), "us_per_launch": round(t * 1e6, 2),
+            "compulsory_bytes": comp, "achieved_gbs": round(comp / t / 1e9, 1),
+            "time_roofline_frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": hbsrc}
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(w, napply):
+    """The FP64 CPU oracle's Schur operator on the same lattice: napply
+    applications (2 hopping terms each) timed on the host cores."""
+    import oracle
+    import synth
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    U = synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])
+    psi = synth.gaussian_spinor(dims, w["src_seed"])
+    A = oracle.clover(U, w["kappa"], w["csw"])
+    Ainv, _ = oracle.invert_site_matrices(A)
+    oracle.schur(U, A, Ainv, w["kappa"], psi)  # touch memory once
+    times = []
+    for _ in range(napply):
+        t0 = time.perf_counter()
+        oracle.schur(U, A, Ainv, w["kappa"], psi)
+        times.append(time.perf_counter() - t0)
+    flops_per = 2 * 1320.0 * (V // 2)
+    return {"times": times, "gflops": flops_per * len(times) / sum(times) / 1e9,
+            "cores": os.cpu_count()}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    o = oracle_sample(w, args.warmup + args.steps)
+    times = o["times"][args.warmup:]
+    V = int(np.prod(w["dims"]))
+    val = 2 * 1320.0 * (V // 2) * len(times) / sum(times) / 1e9
+    sample = ("%d applications of the oracle's even-odd Schur operator (2 hopping terms each) on the "
+              "full %s lattice, FP64, OpenMP" % (len(times), "x".join(map(str, w["dims"]))))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(w), "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": o["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--quick", action="store_true", help="skip the comparison legs")
+    ap.add_argument("--cpu-applications", type=int, default=3)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_ours(args, w, rank, world, local_rank)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.quick:
+            o = oracle_sample(w, args.cpu_applications)
+            cpu = {"value": o["gflops"], "unit": "GFLOP/s", "cores": o["cores"], "kind": "oracle",
+                   "sample": "%d applications of the oracle's even-odd Schur operator (2 hopping terms "
+                             "each) on the full %s lattice, FP64, OpenMP on all host cores"
+                             % (args.cpu_applications, "x".join(map(str, w["dims"])))}
+        ms_step = r["ms"] / args.steps
+        line = {
+            "metric": METRIC, "value": round(r["value"], 2), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "storage": "f16 spinors/links/clover with per-site norm; f64 reliable updates",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w), "inner": "f16", "reliable_update_every": 50,
+                       "recon": 12, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (working set > 1 GB per solve)"},
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r.get("e2e"),
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "solve_per_step": {"iterations": r["stats"][-1]["iterations"],
+                               "reliable_updates": r["stats"][-1]["reliable_updates"],
+                               "dslash": r["stats"][-1]["dslash_count"],
+                               "true_residual_max": r["worst_res"]},
+            "clover_setup_s": r["clover_setup_s"],
+            "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * lqcd.h - C ABI of the GB300 Wilson-clover Dirac operator and solver library.
+ *
+ * The library applies the Wilson(-clover) Dirac operator M and solves
+ * M x = b through CG on the normal equations of the even-odd Schur
+ * complement, the problem the paper states as M phi = b or
+ * M^dag M phi = b (Sec. 3, Eq. (1)) and solves with CG in Sec. 5.
+ *
+ * Conventions (fixed; the paper uses the standard Wilson formulation
+ * without writing it out):
+ *   H psi(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)
+ *   A(x)     = 1 + i kappa csw sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu}(x)   (clover)
+ *   M        = A - kappa H
+ *   Mhat     = A_oo - kappa^2 H_oe A_ee^{-1} H_eo       (odd-parity Schur complement)
+ * DeGrand-Rossi (chiral) gamma matrices, sigma_{mu nu} = (i/2)[g_mu, g_nu],
+ * Fhat = (Q - Q^dag)/8 made traceless with Q the sum of the four plaquette
+ * leaves, periodic boundaries in x, y, z, and a factor -1 on every fermion
+ * hop across the t boundary when t_antiperiodic is set.  Parity of a site is
+ * (x + y + z + t) mod 2, even = 0, odd = 1.
+ *
+ * Canonical layouts (FP64, what users hand in and get back):
+ *   gauge   U[t][z][y][x][mu][a][b][re,im]   mu = 0..3 for x, y, z, t
+ *   spinor  psi[t][z][y][x][spin][colour][re,im]
+ * Internal layouts (what lqcd_dslash / lqcd_clover_apply take; produced by
+ * lqcd_pack): one field per parity, structure of arrays over the V/2 sites
+ * of that parity in 16-byte vectors; lqcd_field_bytes gives the size.
+ *   F64:      12 chunks of double2 (one complex each), [chunk][stride]
+ *   F32:       6 chunks of float4 (two complex each),  [chunk][stride]
+ *   F16/BF16:  3 chunks of 8 halves (four complex each), [chunk][stride],
+ *              followed by one FP32 per-site norm [stride]; the stored
+ *              value is q = v / n with n = max |v_i| over the 24 reals.
+ * stride = V/2 rounded up to a multiple of 128.  A "full" internal field is
+ * the even field followed by the odd field.  nrhs fields are stored back
+ * to back.
+ *
+ * Memory: the library never allocates device memory.  All persistent
+ * state (gauge copies, clover, solver vectors, reduction scratch) lives
+ * in one caller-owned workspace (lqcd_workspace_size / lqcd_set_workspace),
+ * typically a torch tensor.  Vectors handed to calls are caller-owned too.
+ *
+ * Errors: every call returns an lqcd_status and never throws.  A
+ * human-readable message for the last failure on the calling thread is
+ * available from lqcd_last_error().  Calls are asynchronous on the
+ * context's stream; device-side problems (a singular clover block, a solver
+ * breakdown) are recorded in a device error word and reported by lqcd_sync
+ * or at the end of a solve.  A context is not thread-safe; separate
+ * contexts may be used concurrently.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+typedef enum {
+    LQCD_OK = 0,
+    LQCD_ERR_INVALID = 1,         /* bad argument (pointer, parity, size, flag) */
+    LQCD_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+    LQCD_ERR_NOMEM = 3,           /* workspace missing or too small */
+    LQCD_ERR_STATE = 4,           /* call out of order (no gauge, csw mismatch ...) */
+    LQCD_ERR_NOT_CONVERGED = 5,   /* solver hit maxiter; x holds the partial solution */
+    LQCD_ERR_BREAKDOWN = 6,       /* solver produced NaN/Inf or diverged */
+    LQCD_ERR_TIMEOUT = 7,         /* a bounded device wait expired */
+    LQCD_ERR_CLOVER_SINGULAR = 8  /* some 6x6 clover block has |pivot| < 1e-12 */
+} lqcd_status;
+
+typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3 } lqcd_prec;
+
+/* operator selection for lqcd_dslash (op_flags) */
+enum {
+    LQCD_OP_HOP = 0,    /* out_p = H_{p,1-p} in_{1-p}; kappa, csw ignored */
+    LQCD_OP_SCHUR = 1,  /* out_o = Mhat in_o; parity must be 1 (odd) */
+    LQCD_OP_FULL = 2,   /* out = M in on full internal fields; parity ignored */
+    LQCD_DAG = 1 << 8   /* apply the adjoint (H^dag = g5 H g5, Mhat^dag, M^dag) */
+};
+
+typedef struct {
+    int dims[4];          /* Lx, Ly, Lz, Lt; each even and >= 2 */
+    int t_antiperiodic;   /* 1: factor -1 on fermion hops across the t boundary */
+    int recon;            /* 12 or 18: link storage for F32/F16/BF16 (F64 always 18) */
+    int prec_mask;        /* bit (1 << lqcd_prec) for each precision to hold; F64 is always held */
+    int max_nrhs;         /* largest nrhs used with the solver vectors (>= 1) */
+    int gcr_nkrylov;      /* Krylov space of FGCR (0: no FGCR vectors reserved) */
+} lqcd_config;
+
+/* Create a context for one lattice.  `cuda_stream` is a cudaStream_t (may
+ * be NULL for the legacy default stream).  No device memory is touched
+ * until lqcd_set_workspace. */
+lqcd_status lqcd_create(const lqcd_config* cfg, void* cuda_stream, lqcd_ctx** out);
+lqcd_status lqcd_destroy(lqcd_ctx* ctx);
+lqcd_status lqcd_set_stream(lqcd_ctx* ctx, void* cuda_stream);
+
+/* Bytes of device workspace the context needs (256-byte aligned base). */
+lqcd_status lqcd_workspace_size(const lqcd_ctx* ctx, size_t* bytes);
+/* Hand the context its workspace (caller-owned, must outlive the context). */
+lqcd_status lqcd_set_workspace(lqcd_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Bytes of one internal single-parity field of precision `prec`. */
+lqcd_status lqcd_field_bytes(const lqcd_ctx* ctx, lqcd_prec prec, size_t* bytes);
+
+/* Load the gauge field (canonical FP64, host or device pointer; detected)
+ * and build every internal copy (F64 recon-18, the others with cfg.recon).
+ * Invalidates the clover term. */
+lqcd_status lqcd_gauge_load(lqcd_ctx* ctx, const double* links);
+
+/* Build the clover term A and A^{-1} on both parities for (kappa, csw)
+ * from the loaded links: four-leaf Fhat, two 6x6 Hermitian blocks per site,
+ * computed and inverted in FP64 (Gauss-Jordan with partial pivoting), then
+ * rounded into every held precision.  csw = 0 gives A = 1 (nothing stored
+ * is read).  Returns LQCD_ERR_CLOVER_SINGULAR if some block is singular. */
+lqcd_status lqcd_clover_compute(lqcd_ctx* ctx, double kappa, double csw);
+
+/* Canonical FP64 spinor(s) (host or device) <-> internal field(s) of one
+ * parity (parity 0/1) or of both (parity -1: full internal field).
+ * nrhs canonical spinors are back to back; so are the internal fields. */
+lqcd_status lqcd_pack(lqcd_ctx* ctx, void* internal, const double* canonical, int parity,
+                      lqcd_prec prec, int nrhs);
+lqcd_status lqcd_unpack(lqcd_ctx* ctx, double* canonical, const void* internal, int parity,
+                        lqcd_prec prec, int nrhs);
+
+/* Apply the operator selected by op_flags to nrhs internal fields (device
+ * pointers, precision prec).  For LQCD_OP_HOP `in` has parity 1-parity
+ * and `out` parity `parity`.  For LQCD_OP_SCHUR and LQCD_OP_FULL, kappa
+ * and csw must be those of the last lqcd_clover_compute (csw = 0 without
+ * one); otherwise LQCD_ERR_STATE.  `out` must not alias `in`. */
+lqcd_status lqcd_dslash(lqcd_ctx* ctx, void* out, const void* in, int parity, double kappa,
+                        double csw, int op_flags, lqcd_prec prec, int nrhs);
+
+/* out_p = A_pp in_p (inverse = 0) or A_pp^{-1} in_p (inverse = 1) on
+ * nrhs internal fields of parity `parity`.  Needs lqcd_clover_compute. */
+lqcd_status lqcd_clover_apply(lqcd_ctx* ctx, void* out, const void* in, int parity, int inverse,
+                              lqcd_prec prec, int nrhs);
+
+typedef enum {
+    LQCD_SOLVER_CG_EO = 0,   /* CG on Mhat^dag Mhat (even-odd), reconstruct x_e */
+    LQCD_SOLVER_CG_FULL = 1, /* CG on M^dag M over the full lattice (CGNR) */
+    LQCD_SOLVER_FGCR = 2     /* flexible GCR(nkrylov) on M, right preconditioned */
+} lqcd_solver_kind;
+
+typedef struct {
+    int solver;              /* lqcd_solver_kind */
+    int inner_prec;          /* lqcd_prec of the inner iteration (F64 = plain FP64 CG) */
+    int maxiter;             /* total inner iterations allowed */
+    int reliable_interval;   /* FP64 residual replacement every this many iterations (0: off) */
+    double reliable_delta;   /* ... or when |r| < delta * max |r| since the last one */
+    int check_interval;      /* host reads the residual every this many iterations */
+    int nkrylov;             /* FGCR restart length */
+    int use_graph;           /* 1: replay the iteration block as a CUDA graph */
+} lqcd_solver_params;
+
+typedef struct {
+    int iterations;          /* inner iterations (all right-hand sides: the maximum) */
+    int reliable_updates;    /* FP64 residual replacements performed */
+    int restarts;            /* FGCR restarts / CG true-residual re-checks */
+    long dslash_count;       /* single-parity hopping applications (all precisions) */
+    long kernel_launches;    /* kernels launched by the call (graph replays count their nodes) */
+    double true_residual;    /* |b - M x| / |b| in FP64 on the device (max over rhs) */
+    double seconds;          /* wall time of the call */
+} lqcd_solver_stats;
+
+/* Defaults: CG_EO, F32 inner, maxiter 100000, reliable every 50, delta 0.1,
+ * check every 10, nkrylov 20, no graph. */
+lqcd_status lqcd_solver_params_default(lqcd_solver_params* p);
+
+/* Solve M x = b for nrhs canonical FP64 right-hand sides (host or device
+ * pointers, back to back) to |b - M x| / |b| <= tol, using the clover
+ * term of the last lqcd_clover_compute (kappa from there; csw = 0 without
+ * one).  x is overwritten (initial guess 0).  The true residual is
+ * recomputed in FP64 at the end.  LQCD_ERR_NOT_CONVERGED leaves the
+ * partial solution in x. */
+lqcd_status lqcd_solve(lqcd_ctx* ctx, double* x, const double* b, double tol, int nrhs,
+                       const lqcd_solver_params* params, lqcd_solver_stats* stats);
+
+/* Wait for the context's stream and report device-side errors. */
+lqcd_status lqcd_sync(lqcd_ctx* ctx);
+
+/* Kernel timing.  While enabled, every hopping-term launch the context
+ * issues is bracketed by CUDA events on its stream (graph replays are not
+ * recorded).  lqcd_profile_read waits for the stream and returns, for each
+ * storage precision (index lqcd_prec), the launches since the last read,
+ * their summed device time, and their algorithmic bytes and flops: bytes
+ * count every input field, link, clover entry and output of the launch
+ * once per output site (the compulsory traffic), flops count 1320 per
+ * output site and right-hand side (the hopping term alone). */
+typedef struct {
+    long launches;
+    double ms;
+    double bytes;
+    double flops;
+} lqcd_profile_entry;
+lqcd_status lqcd_profile_enable(lqcd_ctx* ctx, int enable);
+lqcd_status lqcd_profile_read(lqcd_ctx* ctx, lqcd_profile_entry out[4]);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* lqcd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

@@ -1,0 +1,295 @@
+// Wilson hopping term ("dslash") on one parity, with fused epilogues.
+//
+//   out_p(x) = epi( sum_mu (1 - g_mu) U_mu(x) in(x+mu) + (1 + g_mu) U_mu(x-mu)^dag in(x-mu) )
+//
+// (the matrix-vector product the paper identifies as the dominant cost of
+// every Krylov solver, Sec. 3 and Sec. 5; even-odd splitting makes each
+// application touch one parity of output and the other of input, Sec. 5).
+//
+// One thread per output site.  Every neighbour spinor is spin-projected to
+// a half spinor (two colour vectors) before the SU(3) multiply and
+// reconstructed afterwards, which is the 1320-flop form of the operator.
+// The adjoint (DAG) swaps the projectors, since H^dag = g5 H g5.  The t
+// boundary sign multiplies the half spinor of hops that cross t = Lt-1 <-> 0.
+//
+// Epilogues, in the compute precision:
+//   EPI_NONE     out = a * D
+//   EPI_CLOVINV  out = a * Cl D                  (Cl = A^{-1} of the output parity)
+//   EPI_XPAY     out = Cl y + a * D               (Cl = A, or 1 without clover)
+//   EPI_CG       s = Cl y + a * D; x += alpha p; r -= alpha s  (s never stored)
+// and optionally (RED) the grid sum of |out|^2 (|r|^2 for EPI_CG) in FP64.
+#pragma once
+#include "core.cuh"
+
+namespace lqcd {
+
+enum Epi { EPI_NONE = 0, EPI_CLOVINV = 1, EPI_XPAY = 2, EPI_CG = 3 };
+
+struct DslashArgs {
+    Geom g;
+    int par;                 // output parity
+    void* out;               // output fields (EPI_CG: unused)
+    size_t out_rb;           // bytes between right-hand sides
+    const void* in;          // input fields, parity 1 - par
+    size_t in_rb;
+    const void* gauge;       // gauge copy of this precision / recon
+    const void* clov;        // clover field of the output parity, or nullptr (= 1)
+    const void* y;           // EPI_XPAY / EPI_CG: field of the output parity
+    size_t y_rb;
+    double a;                // coefficient of the hopping term
+    // reductions (RED): per rhs r, partials + r * part_rs, tickets[r], red + r * red_rs
+    double* partials;
+    size_t part_rs;
+    unsigned* tickets;
+    double* red;
+    size_t red_rs;
+    // EPI_CG: x, r in the accumulation precision; p in P; scalars per rhs
+    void* x;
+    void* r;
+    size_t acc_rb;
+    const void* p;
+    size_t p_rb;
+    const double* scal;      // per rhs: scal + r * scal_rs
+    size_t scal_rs;
+    int s_num, s_num2;       // alpha = (scal[s_num] + scal[s_num2]) / (scal[s_den] + scal[s_den2])
+    int s_den, s_den2;
+    const int* skip;         // per rhs: nonzero = converged, do nothing (may be nullptr)
+};
+
+// ---- spin projection (1 + S g_mu), S = -1 or +1, onto two colour vectors
+template <int MU, int S, class R>
+__device__ __forceinline__ void project(const R v[24], R h[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R p0r = v[2 * c], p0i = v[2 * c + 1];
+        const R p1r = v[2 * (3 + c)], p1i = v[2 * (3 + c) + 1];
+        const R p2r = v[2 * (6 + c)], p2i = v[2 * (6 + c) + 1];
+        const R p3r = v[2 * (9 + c)], p3i = v[2 * (9 + c) + 1];
+        R h0r, h0i, h1r, h1i;
+        if (MU == 0) {        // h0 = p0 + S i p3, h1 = p1 + S i p2
+            h0r = p0r - S * p3i; h0i = p0i + S * p3r;
+            h1r = p1r - S * p2i; h1i = p1i + S * p2r;
+        } else if (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
+            h0r = p0r - S * p3r; h0i = p0i - S * p3i;
+            h1r = p1r + S * p2r; h1i = p1i + S * p2i;
+        } else if (MU == 2) { // h0 = p0 + S i p2, h1 = p1 - S i p3
+            h0r = p0r - S * p2i; h0i = p0i + S * p2r;
+            h1r = p1r + S * p3i; h1i = p1i - S * p3r;
+        } else {              // h0 = p0 + S p2, h1 = p1 + S p3
+            h0r = p0r + S * p2r; h0i = p0i + S * p2i;
+            h1r = p1r + S * p3r; h1i = p1i + S * p3i;
+        }
+        h[2 * c] = h0r; h[2 * c + 1] = h0i;
+        h[2 * (3 + c)] = h1r; h[2 * (3 + c) + 1] = h1i;
+    }
+}
+
+// ---- reconstruct the lower spins from the two rotated colour vectors
+template <int MU, int S, class R>
+__device__ __forceinline__ void accumulate(R acc[24], const R w[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R w0r = w[2 * c], w0i = w[2 * c + 1];
+        const R w1r = w[2 * (3 + c)], w1i = w[2 * (3 + c) + 1];
+        acc[2 * c] += w0r; acc[2 * c + 1] += w0i;
+        acc[2 * (3 + c)] += w1r; acc[2 * (3 + c) + 1] += w1i;
+        R r2r, r2i, r3r, r3i;
+        if (MU == 0) {        // r2 = -S i w1, r3 = -S i w0
+            r2r = S * w1i; r2i = -S * w1r;
+            r3r = S * w0i; r3i = -S * w0r;
+        } else if (MU == 1) { // r2 = S w1, r3 = -S w0
+            r2r = S * w1r; r2i = S * w1i;
+            r3r = -S * w0r; r3i = -S * w0i;
+        } else if (MU == 2) { // r2 = -S i w0, r3 = S i w1
+            r2r = S * w0i; r2i = -S * w0r;
+            r3r = -S * w1i; r3i = S * w1r;
+        } else {              // r2 = S w0, r3 = S w1
+            r2r = S * w0r; r2i = S * w0i;
+            r3r = S * w1r; r3i = S * w1i;
+        }
+        acc[2 * (6 + c)] += r2r; acc[2 * (6 + c) + 1] += r2i;
+        acc[2 * (9 + c)] += r3r; acc[2 * (9 + c) + 1] += r3i;
+    }
+}
+
+// w = U h (ADJ = false) or U^dag h (ADJ = true) for both colour vectors of h
+template <bool ADJ, class R>
+__device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[12])
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int k = ADJ ? 2 * (3 * b + a) : 2 * (3 * a + b);
+                const R ur = u[k], ui = ADJ ? -u[k + 1] : u[k + 1];
+                const R hr = h[2 * (3 * s + b)], hi = h[2 * (3 * s + b) + 1];
+                re += ur * hr - ui * hi;
+                im += ur * hi + ui * hr;
+            }
+            w[2 * (3 * s + a)] = re;
+            w[2 * (3 * s + a) + 1] = im;
+        }
+    }
+}
+
+template <int P, int RECON, int MU, bool DAG>
+__device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int i, int full, const int c[4],
+                                        int stepmu, typename RealT<P>::type acc[24])
+{
+    typedef typename RealT<P>::type R;
+    const int L = A.g.L[MU];
+    const int fwd = (c[MU] == L - 1) ? full - (L - 1) * stepmu : full + stepmu;
+    const int bwd = (c[MU] == 0) ? full + (L - 1) * stepmu : full - stepmu;
+    const bool tb = (MU == 3) && A.g.tanti;
+    R v[24], h[12], u[18], w[12];
+    // forward: (1 - g) U_mu(x) in(x + mu)   [dagger: (1 + g)]
+    SpinorIO<P>::load(in, A.g.stride, fwd >> 1, v);
+    project<MU, DAG ? +1 : -1>(v, h);
+    if (tb && c[3] == L - 1) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) h[k] = -h[k];
+    }
+    GaugeIO<P, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
+    su3_mul_half<false>(u, h, w);
+    accumulate<MU, DAG ? +1 : -1>(acc, w);
+    // backward: (1 + g) U_mu(x - mu)^dag in(x - mu)   [dagger: (1 - g)]
+    SpinorIO<P>::load(in, A.g.stride, bwd >> 1, v);
+    project<MU, DAG ? -1 : +1>(v, h);
+    if (tb && c[3] == 0) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) h[k] = -h[k];
+    }
+    GaugeIO<P, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
+    su3_mul_half<true>(u, h, w);
+    accumulate<MU, DAG ? -1 : +1>(acc, w);
+}
+
+template <int P, int RECON, bool DAG, int EPI, bool RED>
+__global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
+{
+    typedef typename RealT<P>::type R;
+    const int rhs = blockIdx.y;
+    if (A.skip && A.skip[rhs]) return;  // uniform over the rhs: no block of it reduces
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < A.g.Vh;
+    double nrm = 0.0;
+    if (active) {
+        int c[4];
+        cb_coords(A.g, i, A.par, c);
+        const int full = full_index(A.g, c);
+        const char* in = static_cast<const char*>(A.in) + rhs * A.in_rb;
+        R acc[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc[k] = 0;
+        hop_dir<P, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
+        hop_dir<P, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
+        hop_dir<P, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
+        hop_dir<P, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+        const R a = (R)A.a;
+        const int cpar = A.par;  // clover fields are passed per output parity already
+        (void)cpar;
+        if (EPI == EPI_NONE) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc[k] *= a;
+        } else if (EPI == EPI_CLOVINV) {
+            if (A.clov) {
+                R t[24];
+                clover_apply_site<P>(A.clov, A.g.stride, i, acc, t);
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc[k] = a * t[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc[k] *= a;
+            }
+        } else {  // EPI_XPAY, EPI_CG
+            R yv[24], t[24];
+            SpinorIO<P>::load(static_cast<const char*>(A.y) + rhs * A.y_rb, A.g.stride, i, yv);
+            if (A.clov) {
+                clover_apply_site<P>(A.clov, A.g.stride, i, yv, t);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) t[k] = yv[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc[k] = t[k] + a * acc[k];
+        }
+        if (EPI == EPI_CG) {
+            typedef typename RealT<AccumP<P>::value>::type RA;
+            const double* sc = A.scal + rhs * A.scal_rs;
+            const RA alpha = (RA)((sc[A.s_num] + sc[A.s_num2]) / (sc[A.s_den] + sc[A.s_den2]));
+            R pv[24];
+            RA xv[24], rv[24];
+            SpinorIO<P>::load(static_cast<const char*>(A.p) + rhs * A.p_rb, A.g.stride, i, pv);
+            char* xb = static_cast<char*>(A.x) + rhs * A.acc_rb;
+            char* rb = static_cast<char*>(A.r) + rhs * A.acc_rb;
+            SpinorIO<AccumP<P>::value>::load(xb, A.g.stride, i, xv);
+            SpinorIO<AccumP<P>::value>::load(rb, A.g.stride, i, rv);
+            RA n = 0;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                xv[k] += alpha * (RA)pv[k];
+                rv[k] -= alpha * (RA)acc[k];
+                n += rv[k] * rv[k];
+            }
+            nrm = (double)n;
+            SpinorIO<AccumP<P>::value>::store(xb, A.g.stride, i, xv);
+            SpinorIO<AccumP<P>::value>::store(rb, A.g.stride, i, rv);
+        } else {
+            SpinorIO<P>::store(static_cast<char*>(A.out) + rhs * A.out_rb, A.g.stride, i, acc);
+            if (RED) {
+                R n = 0;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) n += acc[k] * acc[k];
+                nrm = (double)n;
+            }
+        }
+    }
+    if (RED || EPI == EPI_CG) {
+        double v[1] = {nrm};
+        block_reduce_finalize<1>(v, A.partials + rhs * A.part_rs, A.tickets + rhs, A.red + rhs * A.red_rs);
+    }
+}
+
+// Launch helper: grid (ceil(Vh / block), nrhs).
+template <int P, int RECON, bool DAG, int EPI, bool RED>
+cudaError_t launch_dslash_t(const DslashArgs& A, int nrhs, int block, cudaStream_t s)
+{
+    dim3 grid((A.g.Vh + block - 1) / block, nrhs);
+    dslash_kernel<P, RECON, DAG, EPI, RED><<<grid, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+// Runtime dispatch over (recon, dag, epi, red) for a fixed precision P.
+template <int P>
+cudaError_t dispatch_dslash_p(const DslashArgs& A, int recon, bool dag, int epi, bool red, int nrhs, int block,
+                              cudaStream_t s)
+{
+#define LQ_CASE(RC, DG, EP, RD)                                                              \
+    if (recon == RC && dag == DG && epi == EP && red == RD)                                 \
+        return launch_dslash_t<P, RC, DG, EP, RD>(A, nrhs, block, s);
+#define LQ_EPIS(RC, DG)                  \
+    LQ_CASE(RC, DG, EPI_NONE, false)     \
+    LQ_CASE(RC, DG, EPI_CLOVINV, false)  \
+    LQ_CASE(RC, DG, EPI_XPAY, false)     \
+    LQ_CASE(RC, DG, EPI_XPAY, true)      \
+    LQ_CASE(RC, DG, EPI_CG, true)
+    if constexpr (P == P64) {
+        LQ_EPIS(18, false)
+        LQ_EPIS(18, true)
+    } else {
+        LQ_EPIS(12, false)
+        LQ_EPIS(12, true)
+        LQ_EPIS(18, false)
+        LQ_EPIS(18, true)
+    }
+#undef LQ_EPIS
+#undef LQ_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lqcd

@@ -1,0 +1,321 @@
+"""Thin Python binding of the C ABI in include/lqcd.h.
+
+Argument marshalling only: every computation runs in liblqcd.so's CUDA
+kernels.  PyTorch provides device memory (the workspace and the vectors)
+and streams.  The functions keep the C names; ``Lattice`` is a small
+convenience owner of one context and its workspace tensor.
+
+If liblqcd.so has not been built this module raises on import: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqcd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("liblqcd.so is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+
+_lib = C.CDLL(LIB_PATH)
+
+LQCD_OK = 0
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_STATE",
+          5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_CLOVER_SINGULAR"}
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
+SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR = 0, 1, 2
+
+
+class lqcd_config(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("t_antiperiodic", C.c_int), ("recon", C.c_int),
+                ("prec_mask", C.c_int), ("max_nrhs", C.c_int), ("gcr_nkrylov", C.c_int)]
+
+
+class lqcd_solver_params(C.Structure):
+    _fields_ = [("solver", C.c_int), ("inner_prec", C.c_int), ("maxiter", C.c_int),
+                ("reliable_interval", C.c_int), ("reliable_delta", C.c_double),
+                ("check_interval", C.c_int), ("nkrylov", C.c_int), ("use_graph", C.c_int)]
+
+
+class lqcd_solver_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("reliable_updates", C.c_int), ("restarts", C.c_int),
+                ("dslash_count", C.c_long), ("kernel_launches", C.c_long),
+                ("true_residual", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lqcd_profile_entry(C.Structure):
+    _fields_ = [("launches", C.c_long), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+_P, _I, _D, _S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+_SIGS = {
+    "lqcd_create": [C.POINTER(lqcd_config), _P, C.POINTER(_P)],
+    "lqcd_destroy": [_P],
+    "lqcd_set_stream": [_P, _P],
+    "lqcd_workspace_size": [_P, C.POINTER(_S)],
+    "lqcd_set_workspace": [_P, _P, _S],
+    "lqcd_field_bytes": [_P, _I, C.POINTER(_S)],
+    "lqcd_gauge_load": [_P, _P],
+    "lqcd_clover_compute": [_P, _D, _D],
+    "lqcd_pack": [_P, _P, _P, _I, _I, _I],
+    "lqcd_unpack": [_P, _P, _P, _I, _I, _I],
+    "lqcd_dslash": [_P, _P, _P, _I, _D, _D, _I, _I, _I],
+    "lqcd_clover_apply": [_P, _P, _P, _I, _I, _I, _I],
+    "lqcd_solver_params_default": [C.POINTER(lqcd_solver_params)],
+    "lqcd_solve": [_P, _P, _P, _D, _I, C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
+    "lqcd_sync": [_P],
+    "lqcd_profile_enable": [_P, _I],
+    "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.lqcd_last_error.restype = C.c_char_p
+_lib.lqcd_last_error.argtypes = []
+
+EXPORTED = list(_SIGS) + ["lqcd_last_error"]
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.lqcd_last_error().decode()
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), msg))
+
+
+def _check(st, where):
+    if st != LQCD_OK:
+        raise LqcdError(st, where)
+    return st
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (no copy)."""
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    raise TypeError(type(x))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ C-name wrappers
+
+def lqcd_last_error():
+    return _lib.lqcd_last_error().decode()
+
+
+def lqcd_create(dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16"),
+                max_nrhs=1, gcr_nkrylov=0, stream=None):
+    cfg = lqcd_config()
+    for i, d in enumerate(dims):
+        cfg.dims[i] = int(d)
+    cfg.t_antiperiodic = int(t_antiperiodic)
+    cfg.recon = int(recon)
+    cfg.prec_mask = sum(1 << PREC[p] for p in precisions)
+    cfg.max_nrhs = int(max_nrhs)
+    cfg.gcr_nkrylov = int(gcr_nkrylov)
+    ctx = C.c_void_p()
+    _check(_lib.lqcd_create(C.byref(cfg), _stream_handle(stream), C.byref(ctx)), "lqcd_create")
+    return ctx
+
+
+def lqcd_destroy(ctx):
+    _check(_lib.lqcd_destroy(ctx), "lqcd_destroy")
+
+
+def lqcd_set_stream(ctx, stream):
+    _check(_lib.lqcd_set_stream(ctx, _stream_handle(stream)), "lqcd_set_stream")
+
+
+def lqcd_workspace_size(ctx):
+    n = C.c_size_t()
+    _check(_lib.lqcd_workspace_size(ctx, C.byref(n)), "lqcd_workspace_size")
+    return n.value
+
+
+def lqcd_set_workspace(ctx, ws):
+    _check(_lib.lqcd_set_workspace(ctx, _ptr(ws), ws.numel() * ws.element_size()),
+           "lqcd_set_workspace")
+
+
+def lqcd_field_bytes(ctx, prec):
+    n = C.c_size_t()
+    _check(_lib.lqcd_field_bytes(ctx, PREC.get(prec, prec), C.byref(n)), "lqcd_field_bytes")
+    return n.value
+
+
+def lqcd_gauge_load(ctx, links):
+    _check(_lib.lqcd_gauge_load(ctx, _ptr(links)), "lqcd_gauge_load")
+
+
+def lqcd_clover_compute(ctx, kappa, csw):
+    _check(_lib.lqcd_clover_compute(ctx, float(kappa), float(csw)), "lqcd_clover_compute")
+
+
+def lqcd_pack(ctx, internal, canonical, parity, prec, nrhs=1):
+    _check(_lib.lqcd_pack(ctx, _ptr(internal), _ptr(canonical), int(parity), PREC.get(prec, prec),
+                          int(nrhs)), "lqcd_pack")
+
+
+def lqcd_unpack(ctx, canonical, internal, parity, prec, nrhs=1):
+    _check(_lib.lqcd_unpack(ctx, _ptr(canonical), _ptr(internal), int(parity), PREC.get(prec, prec),
+                            int(nrhs)), "lqcd_unpack")
+
+
+def lqcd_dslash(ctx, out, inp, parity, kappa, csw, op_flags, prec, nrhs=1):
+    _check(_lib.lqcd_dslash(ctx, _ptr(out), _ptr(inp), int(parity), float(kappa), float(csw),
+                            int(op_flags), PREC.get(prec, prec), int(nrhs)), "lqcd_dslash")
+
+
+def lqcd_clover_apply(ctx, out, inp, parity, inverse, prec, nrhs=1):
+    _check(_lib.lqcd_clover_apply(ctx, _ptr(out), _ptr(inp), int(parity), int(inverse),
+                                  PREC.get(prec, prec), int(nrhs)), "lqcd_clover_apply")
+
+
+def lqcd_solver_params_default():
+    p = lqcd_solver_params()
+    _check(_lib.lqcd_solver_params_default(C.byref(p)), "lqcd_solver_params_default")
+    return p
+
+
+def lqcd_solve(ctx, x, b, tol, nrhs=1, params=None, raise_on_error=True):
+    """Returns (status, stats dict)."""
+    if params is None:
+        params = lqcd_solver_params_default()
+    st = lqcd_solver_stats()
+    rc = _lib.lqcd_solve(ctx, _ptr(x), _ptr(b), float(tol), int(nrhs), C.byref(params), C.byref(st))
+    if raise_on_error:
+        _check(rc, "lqcd_solve")
+    return rc, st.as_dict()
+
+
+def lqcd_sync(ctx):
+    _check(_lib.lqcd_sync(ctx), "lqcd_sync")
+
+
+def lqcd_profile_enable(ctx, enable=True):
+    _check(_lib.lqcd_profile_enable(ctx, int(bool(enable))), "lqcd_profile_enable")
+
+
+def lqcd_profile_read(ctx):
+    """{prec name: {launches, ms, bytes, flops}} since the last read."""
+    arr = (lqcd_profile_entry * 4)()
+    _check(_lib.lqcd_profile_read(ctx, arr), "lqcd_profile_read")
+    names = ("f64", "f32", "f16", "bf16")
+    return {names[i]: {k: getattr(arr[i], k) for k, _ in lqcd_profile_entry._fields_}
+            for i in range(4)}
+
+
+def solver_params(**kw):
+    p = lqcd_solver_params_default()
+    for k, v in kw.items():
+        if k == "inner_prec":
+            v = PREC.get(v, v)
+        setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------- convenience
+
+class Lattice:
+    """One context + its workspace (a torch uint8 tensor on ``device``)."""
+
+    def __init__(self, dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16"),
+                 max_nrhs=1, gcr_nkrylov=0, device="cuda", stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.device = torch.device(device)
+        self.stream = stream
+        with torch.cuda.device(self.device):
+            self.ctx = lqcd_create(self.dims, t_antiperiodic, recon, precisions, max_nrhs,
+                                   gcr_nkrylov, stream)
+            n = lqcd_workspace_size(self.ctx)
+            self.workspace = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+            off = (-self.workspace.data_ptr()) % 256
+            self._ws_view = self.workspace[off:off + n]
+            lqcd_set_workspace(self.ctx, self._ws_view)
+        self.volume = int(np.prod(self.dims))
+
+    def close(self):
+        if self.ctx is not None:
+            lqcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_bytes(self, prec):
+        return lqcd_field_bytes(self.ctx, prec)
+
+    def new_field(self, prec, nrhs=1, full=False):
+        """Uninitialised internal field(s) as a uint8 device tensor."""
+        n = self.field_bytes(prec) * (2 if full else 1) * nrhs
+        return torch.empty(n, dtype=torch.uint8, device=self.device)
+
+    def canonical_spinor(self, nrhs=1, host=False, pin=False):
+        lx, ly, lz, lt = self.dims
+        shp = ((nrhs,) if nrhs > 1 else ()) + (lt, lz, ly, lx, 4, 3)
+        if host:
+            return torch.zeros(shp, dtype=torch.complex128, pin_memory=pin)
+        return torch.zeros(shp, dtype=torch.complex128, device=self.device)
+
+    def gauge_load(self, links):
+        lqcd_gauge_load(self.ctx, _as_tensor(links, self.device))
+
+    def clover_compute(self, kappa, csw):
+        lqcd_clover_compute(self.ctx, kappa, csw)
+
+    def pack(self, internal, canonical, parity, prec, nrhs=1):
+        lqcd_pack(self.ctx, internal, _as_tensor(canonical, self.device), parity, prec, nrhs)
+
+    def unpack(self, canonical, internal, parity, prec, nrhs=1):
+        lqcd_unpack(self.ctx, canonical, internal, parity, prec, nrhs)
+
+    def dslash(self, out, inp, parity, kappa=0.0, csw=0.0, op=OP_HOP, dag=False, prec="f32", nrhs=1):
+        lqcd_dslash(self.ctx, out, inp, parity, kappa, csw, op | (DAG if dag else 0), prec, nrhs)
+
+    def clover_apply(self, out, inp, parity, inverse, prec="f32", nrhs=1):
+        lqcd_clover_apply(self.ctx, out, inp, parity, inverse, prec, nrhs)
+
+    def solve(self, x, b, tol=1e-10, nrhs=1, raise_on_error=True, **kw):
+        return lqcd_solve(self.ctx, x, b, tol, nrhs, solver_params(**kw), raise_on_error)
+
+    def sync(self):
+        lqcd_sync(self.ctx)
+
+
+def _as_tensor(a, device):
+    """numpy complex128 -> device tensor; tensors pass through."""
+    if isinstance(a, torch.Tensor):
+        return a.contiguous()
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device)

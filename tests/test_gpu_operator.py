@@ -1,0 +1,187 @@
+"""GPU parity of the hopping term, clover term, Schur complement and full
+operator against the FP64 CPU oracle, element by element (rel-L2 over all
+real components, in FP64).
+
+Tolerances: FP64 1e-13 (1e-12 where an inverted clover block enters);
+FP32 1e-6 (the requirement on the FP32 dslash); FP16 / BF16 storage with a
+per-site norm: 3e-3 / 2e-2, i.e. a few units of the format's rounding
+(2^-11, 2^-8) - their errors are also printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import (gauge, gpu_apply, hop_ref, parity_mask, rel, require_cuda,
+                               restrict)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2}
+
+# several tiles with a ragged tail (Vh = 288, 1152+...), the 2^4 degenerate
+# lattice (x+mu = x-mu), and a non-cubic shape
+LATTICES = [(2, 2, 2, 2), (6, 4, 4, 6), (8, 4, 6, 4), (8, 8, 8, 16)]
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_cuda()
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("recon", [12, 18])
+def test_hop_all_precisions(lq, dims, recon):
+    U = gauge(dims, "haar", seed=3)
+    psi = synth.gaussian_spinor(dims, 4)
+    lat = lq.Lattice(dims, recon=recon)
+    lat.gauge_load(U)
+    for prec in ("f64", "f32", "f16", "bf16"):
+        for par in (0, 1):
+            for dag in (False, True):
+                got = gpu_apply(lat, prec, psi, 1 - par, par,
+                                lambda o, i: lat.dslash(o, i, par, prec=prec, dag=dag))
+                want = hop_ref(U, psi, dims, par, dag)
+                err = rel(got, want)
+                print("hop %s recon %d par %d dag %d: %.3e" % (prec, recon, par, dag, err))
+                assert err < TOL[prec], (prec, par, dag, err)
+
+
+def test_hop_periodic_t(lq):
+    dims = (4, 4, 4, 6)
+    U = gauge(dims, "haar", seed=5)
+    psi = synth.gaussian_spinor(dims, 6)
+    lat = lq.Lattice(dims, t_antiperiodic=0)
+    lat.gauge_load(U)
+    got = gpu_apply(lat, "f64", psi, 1, 0, lambda o, i: lat.dslash(o, i, 0, prec="f64"))
+    src = restrict(psi, dims, 1)
+    want = restrict(oracle.hop(U, src, tanti=0), dims, 0)
+    assert rel(got, want) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_clover_apply(lq, prec):
+    dims = (6, 4, 4, 8)
+    kappa, csw = 0.135, 1.0
+    U = gauge(dims, "smooth", seed=7)
+    psi = synth.gaussian_spinor(dims, 8)
+    lat = lq.Lattice(dims)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    A = oracle.clover(U, kappa, csw)
+    Ainv, bad = oracle.invert_site_matrices(A)
+    assert bad == 0
+    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2}[prec]
+    for par in (0, 1):
+        for inv, M in ((0, A), (1, Ainv)):
+            got = gpu_apply(lat, prec, psi, par, par,
+                            lambda o, i: lat.clover_apply(o, i, par, inv, prec=prec))
+            want = restrict(oracle.apply_site_matrices(M, psi), dims, par)
+            err = rel(got, want)
+            print("clover %s par %d inv %d: %.3e" % (prec, par, inv, err))
+            assert err < tol
+
+
+@pytest.mark.parametrize("dims,kind", [((4, 4, 4, 4), "haar"), ((8, 6, 4, 6), "smooth"),
+                                       ((16, 16, 16, 32), "smooth")])
+def test_schur_and_full_operator(lq, dims, kind):
+    """Mhat (odd Schur complement, clover) and M, with and without dagger.
+    16^3x32 is the even-odd Wilson-clover FP32 workload (kappa 0.135, csw 1)."""
+    kappa, csw = 0.135, 1.0
+    U = gauge(dims, kind, seed=9)
+    psi = synth.gaussian_spinor(dims, 10)
+    lat = lq.Lattice(dims)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    A = oracle.clover(U, kappa, csw)
+    Ainv, _ = oracle.invert_site_matrices(A)
+    precs = ("f64", "f32") if dims[3] >= 32 else ("f64", "f32", "f16", "bf16")
+    for prec in precs:
+        tol = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 3e-2}[prec]
+        for dag in (False, True):
+            got = gpu_apply(lat, prec, psi, 1, 1, lambda o, i: lat.dslash(
+                o, i, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec))
+            want = oracle.schur(U, A, Ainv, kappa, psi, dag=dag)
+            err = rel(got, want)
+            print("schur %s dag %d: %.3e" % (prec, dag, err))
+            assert err < tol
+            got = gpu_apply(lat, prec, psi, 0, 0, lambda o, i: lat.dslash(
+                o, i, 0, kappa, csw, op=lq.OP_FULL, dag=dag, prec=prec), full=True)
+            want = oracle.wilson_clover(U, A, kappa, psi, dag=dag)
+            err = rel(got, want)
+            print("full %s dag %d: %.3e" % (prec, dag, err))
+            assert err < tol
+
+
+def test_wilson_without_clover(lq):
+    dims = (4, 4, 4, 8)
+    kappa = 0.12
+    U = gauge(dims, "haar", seed=11)
+    psi = synth.gaussian_spinor(dims, 12)
+    lat = lq.Lattice(dims)
+    lat.gauge_load(U)
+    got = gpu_apply(lat, "f64", psi, 0, 0, lambda o, i: lat.dslash(
+        o, i, 0, kappa, 0.0, op=lq.OP_FULL, prec="f64"), full=True)
+    assert rel(got, oracle.wilson_clover(U, None, kappa, psi)) < 1e-13
+    got = gpu_apply(lat, "f64", psi, 1, 1, lambda o, i: lat.dslash(
+        o, i, 1, kappa, 0.0, op=lq.OP_SCHUR, prec="f64"))
+    assert rel(got, oracle.schur(U, None, None, kappa, psi)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_multi_rhs_matches_single(lq, prec):
+    """nrhs fields in one launch give bit-identical results to one per call."""
+    import torch
+    dims = (8, 4, 4, 8)
+    R = 3
+    U = gauge(dims, "smooth", seed=13)
+    psis = synth.gaussian_spinor(dims, 14, nfields=R)
+    lat = lq.Lattice(dims, max_nrhs=R)
+    lat.gauge_load(U)
+    fb = lat.field_bytes(prec)
+    fin = lat.new_field(prec, nrhs=R)
+    fout = lat.new_field(prec, nrhs=R)
+    lat.pack(fin, psis, 1, prec, nrhs=R)
+    lat.dslash(fout, fin, 0, prec=prec, nrhs=R)
+    single = torch.empty(fb, dtype=torch.uint8, device="cuda")
+    for r in range(R):
+        lat.dslash(single, fin[r * fb:(r + 1) * fb], 0, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(single, fout[r * fb:(r + 1) * fb])
+
+
+def test_pack_roundtrip(lq):
+    dims = (6, 4, 4, 6)
+    psi = synth.gaussian_spinor(dims, 15)
+    lat = lq.Lattice(dims)
+    for prec, tol in (("f64", 0.0), ("f32", 1e-7), ("f16", 1e-3), ("bf16", 8e-3)):
+        f = lat.new_field(prec, full=True)
+        lat.pack(f, psi, -1, prec)
+        out = lat.canonical_spinor()
+        lat.unpack(out, f, -1, prec)
+        import torch
+        torch.cuda.synchronize()
+        assert rel(out.cpu().numpy(), psi) <= tol
+
+
+@pytest.mark.slow
+def test_hop_full_size_sampled(lq):
+    """32^3x64, FP32 recon-12 (the benchmark's dslash): sampled output sites
+    against the oracle computed site by site."""
+    dims = (32, 32, 32, 64)
+    U = gauge(dims, "smooth", seed=3, eps=0.4)
+    psi = synth.gaussian_spinor(dims, 0)
+    lat = lq.Lattice(dims, precisions=("f64", "f32"))
+    lat.gauge_load(U)
+    rng = np.random.default_rng(0)
+    for par in (0, 1):
+        got = gpu_apply(lat, "f32", psi, 1 - par, par, lambda o, i: lat.dslash(o, i, par, prec="f32"))
+        src = restrict(psi, dims, 1 - par)
+        mask = parity_mask(dims).reshape(-1)
+        cand = np.nonzero(mask == par)[0]
+        sites = np.sort(rng.choice(cand, 4096, replace=False))
+        want = oracle.hop_sites(U, src, sites)
+        g = got.reshape(-1, 4, 3)[sites]
+        err = rel(g, want)
+        print("full-size hop par %d: %.3e" % (par, err))
+        assert err < 1e-6
