@@ -40,6 +40,8 @@ METRIC = "Dslash GFLOP/s & % HBM roofline; solve time to 1e-10 resid vs plain FP
 WORKLOADS = {
     "32c64": dict(dims=(32, 32, 32, 64), eps=0.4, gauge_seed=3, src_seed=0, kappa=0.1355, csw=1.0),
     "16c32": dict(dims=(16, 16, 16, 32), eps=0.5, gauge_seed=2, src_seed=0, kappa=0.135, csw=1.0),
+    # larger than L2, a few GB on the device: the size used for kernel captures
+    "24c48": dict(dims=(24, 24, 24, 48), eps=0.4, gauge_seed=3, src_seed=0, kappa=0.1355, csw=1.0),
 }
 TOL = 1e-10
 FALLBACK_HBM_GBS = 6800.0
@@ -122,7 +124,8 @@ def run_ours(args, w, rank, world, local_rank):
     U = synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])
     b = synth.gaussian_spinor(dims, w["src_seed"])
     stream = torch.cuda.Stream(device=dev)
-    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16", "bf16"), recon=12, device=dev,
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16", "bf16", "f16links", "bf16links"), recon=12,
+                       device=dev,
                        stream=stream)
     with torch.cuda.stream(stream):
         Ud = torch.from_numpy(U).to(dev)
@@ -134,7 +137,7 @@ def run_ours(args, w, rank, world, local_rank):
     lat.clover_compute(w["kappa"], w["csw"])
     clover_s = time.time() - t0
     del Ud
-    params = dict(inner_prec="f16", reliable_interval=50, check_interval=10)
+    params = dict(inner_prec=args.inner, reliable_interval=50, check_interval=10)
 
     def barrier():
         if world > 1:
@@ -174,9 +177,10 @@ def run_ours(args, w, rank, world, local_rank):
 
     # dominant kernel: the FP16 hopping kernels (all epilogues) inside the solve
     hb, hbsrc = measured_peaks()
-    pf = prof["f16"]
+    pf = prof[args.inner]
     achieved = pf["bytes"] / (pf["ms"] * 1e-3) / 1e9 if pf["ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "dslash_kernel<F16, recon-12> (all epilogues of the solve)",
+    roofline = {"bound": "hbm", "kernel": "dslash_kernel (%s storage, recon-12; all epilogues of the solve)"
+                % args.inner,
                 "achieved": round(achieved, 1), "peak": hb, "unit": "GB/s",
                 "frac": round(achieved / hb, 4), "peak_source": hbsrc,
                 "launches": pf["launches"], "avg_launch_us": round(1e3 * pf["ms"] / max(1, pf["launches"]), 2),
@@ -219,8 +223,10 @@ def compare_solves(lat, bd, xd, stream, params):
     with CUDA events on the context stream."""
     import torch
     res = {}
-    for name, kw in (("f16_inner_f64_ru", dict(params)),
+    for name, kw in (("f16_inner_f64_ru", dict(params, inner_prec="f16")),
                      ("bf16_inner_f64_ru", dict(params, inner_prec="bf16")),
+                     ("f16links_inner_f64_ru", dict(params, inner_prec="f16links")),
+                     ("bf16links_inner_f64_ru", dict(params, inner_prec="bf16links")),
                      ("f32_inner_f64_ru", dict(params, inner_prec="f32")),
                      ("plain_f64_cg", dict(inner_prec="f64", check_interval=10))):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -324,6 +330,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32c64", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip the comparison legs")
+    ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links"],
+                    help="storage of the timed solve's inner iteration")
     ap.add_argument("--cpu-applications", type=int, default=3)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -352,7 +360,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "storage": "f16 spinors/links/clover with per-site norm; f64 reliable updates",
             "data": "synthetic",
-            "config": {"workload": workload_name(w), "inner": "f16", "reliable_update_every": 50,
+            "config": {"workload": workload_name(w), "inner": args.inner, "reliable_update_every": 50,
                        "recon": 12, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set > 1 GB per solve)"},
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r.get("e2e"),

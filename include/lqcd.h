@@ -70,7 +70,22 @@ typedef enum {
     LQCD_ERR_CLOVER_SINGULAR = 8  /* some 6x6 clover block has |pivot| < 1e-12 */
 } lqcd_status;
 
-typedef enum { LQCD_F64 = 0, LQCD_F32 = 1, LQCD_F16 = 2, LQCD_BF16 = 3 } lqcd_prec;
+/* Storage precision of links, clover and spinor fields.  Arithmetic is FP64
+ * for LQCD_F64 and FP32 for every other value.  LQCD_F16_LINKS and
+ * LQCD_BF16_LINKS keep the operator's coefficients (links and clover) in
+ * FP16 / BF16 but every spinor field in the F32 layout: rounding only the
+ * coefficients perturbs the operator by a fixed Hermitian amount that CG
+ * tolerates, while rounding the Krylov vectors to 11 (8) mantissa bits
+ * injects noise that the operator amplifies by its condition number. */
+typedef enum {
+    LQCD_F64 = 0,
+    LQCD_F32 = 1,
+    LQCD_F16 = 2,
+    LQCD_BF16 = 3,
+    LQCD_F16_LINKS = 4,
+    LQCD_BF16_LINKS = 5,
+    LQCD_NPREC = 6
+} lqcd_prec;
 
 /* operator selection for lqcd_dslash (op_flags) */
 enum {
@@ -195,7 +210,7 @@ typedef struct {
     double flops;
 } lqcd_profile_entry;
 lqcd_status lqcd_profile_enable(lqcd_ctx* ctx, int enable);
-lqcd_status lqcd_profile_read(lqcd_ctx* ctx, lqcd_profile_entry out[4]);
+lqcd_status lqcd_profile_read(lqcd_ctx* ctx, lqcd_profile_entry out[LQCD_NPREC]);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* lqcd_last_error(void);

@@ -45,7 +45,7 @@ DslashArgs base_args(lqcd_ctx* c, int P)
     DslashArgs A;
     memset(&A, 0, sizeof(A));
     A.g = c->g;
-    A.gauge = c->gauge[P];
+    A.gauge = c->gauge[mode_pg(P)];
     A.partials = c->partials;
     A.part_rs = c->part_rs;
     A.tickets = c->tickets;
@@ -81,12 +81,13 @@ struct Profiler {
 
 // Compulsory bytes of one launch per output site and right-hand side:
 // input spinor, 8 links, and each epilogue operand once.
-static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int P, int epi)
+static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int mode, int epi)
 {
-    const double S = (double)spinor_field_bytes(P, 1);
-    const double L = (double)gauge_link_bytes(P, c->recon_of(P));
-    const double Cl = A.clov ? (double)clover_site_bytes(P) : 0.0;
-    const double Acc = (double)spinor_field_bytes(AccumPrec(P), 1);
+    const int pg = mode_pg(mode), ps = mode_ps(mode);
+    const double S = (double)spinor_field_bytes(ps, 1);
+    const double L = (double)gauge_link_bytes(pg, c->recon_of(pg));
+    const double Cl = A.clov ? (double)clover_site_bytes(pg) : 0.0;
+    const double Acc = (double)spinor_field_bytes(AccumPrec(ps), 1);
     double b = S + 8 * L;
     switch (epi) {
     case EPI_NONE: b += S; break;
@@ -101,7 +102,7 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
 {
     int block = c->tuned_block[P][dag ? 1 : 0];
     if (block <= 0) block = c->block;
-    const int rc = c->recon_of(P);
+    const int rc = c->recon_of(mode_pg(P));
     Profiler* pr = c->prof;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (pr && pr->on) cudaStreamIsCapturing(c->stream, &cap);
@@ -119,7 +120,9 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
     case P64: e = dslash_dispatch_f64(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case P32: e = dslash_dispatch_f32(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case P16: e = dslash_dispatch_f16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
-    default: e = dslash_dispatch_bf16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    case PB16: e = dslash_dispatch_bf16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    case MODE_F16_LINKS: e = dslash_dispatch_f16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    default: e = dslash_dispatch_bf16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     }
     LQ_CUDA(e);
     if (timed) {
@@ -155,8 +158,9 @@ lqcd_status op_hop(lqcd_ctx* c, void* out, const void* in, int parity, int P, bo
 static const void* clover_ptr(lqcd_ctx* c, int P, int parity, bool inverse)
 {
     if (c->clover_state == 0 || c->csw == 0.0) return nullptr;
-    const char* base = static_cast<const char*>(inverse ? c->clovinv[P] : c->clov[P]);
-    return base + parity * c->clov_parity_bytes(P);
+    const int pg = mode_pg(P);
+    const char* base = static_cast<const char*>(inverse ? c->clovinv[pg] : c->clov[pg]);
+    return base + parity * c->clov_parity_bytes(pg);
 }
 
 // out_o = Mhat in_o = A_oo in_o - kappa^2 H_oe A_ee^{-1} H_eo in_o (dag: Mhat^dag)
@@ -318,11 +322,11 @@ lqcd_status lqcd_profile_enable(lqcd_ctx* c, int enable)
     LQ_GUARD_END
 }
 
-lqcd_status lqcd_profile_read(lqcd_ctx* c, lqcd_profile_entry out[4])
+lqcd_status lqcd_profile_read(lqcd_ctx* c, lqcd_profile_entry out[LQCD_NPREC])
 {
     LQ_GUARD_BEGIN
     if (!c || !out) return fail(LQCD_ERR_INVALID, "lqcd_profile_read: null argument");
-    for (int P = 0; P < 4; ++P) out[P] = lqcd_profile_entry{0, 0.0, 0.0, 0.0};
+    for (int P = 0; P < LQCD_NPREC; ++P) out[P] = lqcd_profile_entry{0, 0.0, 0.0, 0.0};
     if (!c->prof) return LQCD_OK;
     LQ_CUDA(cudaStreamSynchronize(c->stream));
     for (auto& r : c->prof->pending) {
@@ -396,7 +400,7 @@ lqcd_status lqcd_set_workspace(lqcd_ctx* c, void* ptr, size_t bytes)
 lqcd_status lqcd_field_bytes(const lqcd_ctx* c, lqcd_prec prec, size_t* bytes)
 {
     if (!c || !bytes) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: null argument");
-    if (prec < LQCD_F64 || prec > LQCD_BF16) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: bad precision");
+    if (prec < LQCD_F64 || prec >= LQCD_NPREC) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: bad precision");
     *bytes = c->field_bytes(prec);
     return LQCD_OK;
 }
@@ -457,8 +461,8 @@ lqcd_status lqcd_clover_compute(lqcd_ctx* c, double kappa, double csw)
 
 static lqcd_status check_prec(const lqcd_ctx* c, int prec)
 {
-    if (prec < LQCD_F64 || prec > LQCD_BF16) return fail(LQCD_ERR_INVALID, "bad precision");
-    if (!c->holds(prec)) return fail(LQCD_ERR_STATE, "precision not held by this context (cfg.prec_mask)");
+    if (prec < LQCD_F64 || prec >= LQCD_NPREC) return fail(LQCD_ERR_INVALID, "bad precision");
+    if (!c->holds(mode_pg(prec))) return fail(LQCD_ERR_STATE, "precision not held by this context (cfg.prec_mask)");
     return LQCD_OK;
 }
 
@@ -475,8 +479,8 @@ static lqcd_status pack_common(lqcd_ctx* c, void* internal, double* canonical, i
     const size_t canon_rb = (size_t)c->volume * 192;
     const size_t int_rb = (parity < 0 ? 2 : 1) * c->field_bytes(prec);
     if (is_device_ptr(canonical)) {
-        return unpack ? unpack_spinor(c, canonical, internal, parity, prec, nrhs, int_rb, canon_rb)
-                      : pack_spinor(c, internal, canonical, parity, prec, nrhs, int_rb, canon_rb);
+        return unpack ? unpack_spinor(c, canonical, internal, parity, mode_ps(prec), nrhs, int_rb, canon_rb)
+                      : pack_spinor(c, internal, canonical, parity, mode_ps(prec), nrhs, int_rb, canon_rb);
     }
     // host canonical: go through the staging area in chunks of right-hand sides
     const int per = (int)(c->staging_bytes / canon_rb);
@@ -485,13 +489,13 @@ static lqcd_status pack_common(lqcd_ctx* c, void* internal, double* canonical, i
         const int n = nrhs - r0 < per ? nrhs - r0 : per;
         char* in = static_cast<char*>(internal) + r0 * int_rb;
         if (unpack) {
-            LQ_TRY(unpack_spinor(c, static_cast<double*>(c->staging), in, parity, prec, n, int_rb, canon_rb));
+            LQ_TRY(unpack_spinor(c, static_cast<double*>(c->staging), in, parity, mode_ps(prec), n, int_rb, canon_rb));
             LQ_CUDA(cudaMemcpyAsync(canonical + (size_t)r0 * canon_rb / 8, c->staging, n * canon_rb,
                                     cudaMemcpyDeviceToHost, c->stream));
         } else {
             LQ_CUDA(cudaMemcpyAsync(c->staging, canonical + (size_t)r0 * canon_rb / 8, n * canon_rb,
                                     cudaMemcpyHostToDevice, c->stream));
-            LQ_TRY(pack_spinor(c, in, static_cast<const double*>(c->staging), parity, prec, n, int_rb, canon_rb));
+            LQ_TRY(pack_spinor(c, in, static_cast<const double*>(c->staging), parity, mode_ps(prec), n, int_rb, canon_rb));
         }
         LQ_CUDA(cudaStreamSynchronize(c->stream));
     }

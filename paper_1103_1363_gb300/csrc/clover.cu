@@ -331,33 +331,36 @@ lqcd_status clover_build(lqcd_ctx* c, double kappa, double csw)
     return LQCD_OK;
 }
 
-// out = Cl in for one parity, Cl = A or A^{-1}.
-template <int P>
+// out = Cl in for one parity, Cl = A or A^{-1} stored in PG, spinors in PS.
+template <int PG, int PS>
 __global__ void clover_apply_kernel(Geom g, char* out, const char* in, const char* cl, size_t rb)
 {
-    typedef typename RealT<P>::type R;
+    typedef typename RealT<PS>::type R;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int rhs = blockIdx.y;
     if (i >= g.Vh) return;
     R v[24], w[24];
-    SpinorIO<P>::load(in + rhs * rb, g.stride, i, v);
-    clover_apply_site<P>(cl, g.stride, i, v, w);
-    SpinorIO<P>::store(out + rhs * rb, g.stride, i, w);
+    SpinorIO<PS>::load(in + rhs * rb, g.stride, i, v);
+    clover_apply_site<PG>(cl, g.stride, i, v, w);
+    SpinorIO<PS>::store(out + rhs * rb, g.stride, i, w);
 }
 
-lqcd_status clover_apply_launch(lqcd_ctx* c, void* out, const void* in, int parity, int inverse, int P, int nrhs,
+lqcd_status clover_apply_launch(lqcd_ctx* c, void* out, const void* in, int parity, int inverse, int mode, int nrhs,
                                 size_t rb)
 {
     const int block = 128;
     dim3 grid((c->g.Vh + block - 1) / block, nrhs);
-    const char* cl = static_cast<const char*>(inverse ? c->clovinv[P] : c->clov[P]) + parity * c->clov_parity_bytes(P);
+    const int pg = mode_pg(mode);
+    const char* cl = static_cast<const char*>(inverse ? c->clovinv[pg] : c->clov[pg]) + parity * c->clov_parity_bytes(pg);
     char* o = static_cast<char*>(out);
     const char* i = static_cast<const char*>(in);
-    switch (P) {
-    case P64: clover_apply_kernel<P64><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
-    case P32: clover_apply_kernel<P32><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
-    case P16: clover_apply_kernel<P16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
-    default: clover_apply_kernel<PB16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    switch (mode) {
+    case P64: clover_apply_kernel<P64, P64><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    case P32: clover_apply_kernel<P32, P32><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    case P16: clover_apply_kernel<P16, P16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    case PB16: clover_apply_kernel<PB16, PB16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    case MODE_F16_LINKS: clover_apply_kernel<P16, P32><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    default: clover_apply_kernel<PB16, P32><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
     }
     LQ_CUDA(cudaGetLastError());
     c->launches++;

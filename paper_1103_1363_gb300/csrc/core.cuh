@@ -27,6 +27,15 @@ template <> struct RealT<P64> { typedef double type; };
 template <int P> struct AccumP { enum { value = (P == P64) ? P64 : P32 }; };
 __host__ __device__ inline int AccumPrec(int P) { return P == P64 ? P64 : P32; }
 
+// A precision mode selects the storage of the operator's coefficients
+// (links and clover, "pg") and of the spinor fields ("ps").  Modes 0-3 store
+// both in the same precision; modes 4 and 5 store links and clover in FP16 /
+// BF16 and every spinor field in FP32.  The arithmetic is FP64 for mode 0
+// and FP32 otherwise.
+enum { MODE_F16_LINKS = 4, MODE_BF16_LINKS = 5, NMODES = 6 };
+__host__ __device__ inline int mode_pg(int m) { return m == MODE_F16_LINKS ? P16 : m == MODE_BF16_LINKS ? PB16 : m; }
+__host__ __device__ inline int mode_ps(int m) { return m >= MODE_F16_LINKS ? P32 : m; }
+
 // Lattice geometry of one context, passed by value to every kernel.
 struct Geom {
     int L[4];    // Lx, Ly, Lz, Lt

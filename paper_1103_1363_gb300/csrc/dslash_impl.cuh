@@ -137,42 +137,44 @@ __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[1
     }
 }
 
-template <int P, int RECON, int MU, bool DAG>
+// PG: storage of links and clover; PS: storage of spinor fields; the
+// arithmetic is in RealT<PS> (FP64 only when everything is FP64).
+template <int PG, int PS, int RECON, int MU, bool DAG>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int i, int full, const int c[4],
-                                        int stepmu, typename RealT<P>::type acc[24])
+                                        int stepmu, typename RealT<PS>::type acc[24])
 {
-    typedef typename RealT<P>::type R;
+    typedef typename RealT<PS>::type R;
     const int L = A.g.L[MU];
     const int fwd = (c[MU] == L - 1) ? full - (L - 1) * stepmu : full + stepmu;
     const int bwd = (c[MU] == 0) ? full + (L - 1) * stepmu : full - stepmu;
     const bool tb = (MU == 3) && A.g.tanti;
     R v[24], h[12], u[18], w[12];
     // forward: (1 - g) U_mu(x) in(x + mu)   [dagger: (1 + g)]
-    SpinorIO<P>::load(in, A.g.stride, fwd >> 1, v);
+    SpinorIO<PS>::load(in, A.g.stride, fwd >> 1, v);
     project<MU, DAG ? +1 : -1>(v, h);
     if (tb && c[3] == L - 1) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] = -h[k];
     }
-    GaugeIO<P, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
+    GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
     su3_mul_half<false>(u, h, w);
     accumulate<MU, DAG ? +1 : -1>(acc, w);
     // backward: (1 + g) U_mu(x - mu)^dag in(x - mu)   [dagger: (1 - g)]
-    SpinorIO<P>::load(in, A.g.stride, bwd >> 1, v);
+    SpinorIO<PS>::load(in, A.g.stride, bwd >> 1, v);
     project<MU, DAG ? -1 : +1>(v, h);
     if (tb && c[3] == 0) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] = -h[k];
     }
-    GaugeIO<P, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
+    GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
     su3_mul_half<true>(u, h, w);
     accumulate<MU, DAG ? -1 : +1>(acc, w);
 }
 
-template <int P, int RECON, bool DAG, int EPI, bool RED>
+template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
 {
-    typedef typename RealT<P>::type R;
+    typedef typename RealT<PS>::type R;
     const int rhs = blockIdx.y;
     if (A.skip && A.skip[rhs]) return;  // uniform over the rhs: no block of it reduces
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,20 +188,18 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
         R acc[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = 0;
-        hop_dir<P, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
-        hop_dir<P, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
-        hop_dir<P, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
-        hop_dir<P, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+        hop_dir<PG, PS, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
+        hop_dir<PG, PS, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
+        hop_dir<PG, PS, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
+        hop_dir<PG, PS, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
         const R a = (R)A.a;
-        const int cpar = A.par;  // clover fields are passed per output parity already
-        (void)cpar;
         if (EPI == EPI_NONE) {
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] *= a;
         } else if (EPI == EPI_CLOVINV) {
             if (A.clov) {
                 R t[24];
-                clover_apply_site<P>(A.clov, A.g.stride, i, acc, t);
+                clover_apply_site<PG>(A.clov, A.g.stride, i, acc, t);
 #pragma unroll
                 for (int k = 0; k < 24; ++k) acc[k] = a * t[k];
             } else {
@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
             }
         } else {  // EPI_XPAY, EPI_CG
             R yv[24], t[24];
-            SpinorIO<P>::load(static_cast<const char*>(A.y) + rhs * A.y_rb, A.g.stride, i, yv);
+            SpinorIO<PS>::load(static_cast<const char*>(A.y) + rhs * A.y_rb, A.g.stride, i, yv);
             if (A.clov) {
-                clover_apply_site<P>(A.clov, A.g.stride, i, yv, t);
+                clover_apply_site<PG>(A.clov, A.g.stride, i, yv, t);
             } else {
 #pragma unroll
                 for (int k = 0; k < 24; ++k) t[k] = yv[k];
@@ -219,16 +219,16 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
             for (int k = 0; k < 24; ++k) acc[k] = t[k] + a * acc[k];
         }
         if (EPI == EPI_CG) {
-            typedef typename RealT<AccumP<P>::value>::type RA;
+            typedef typename RealT<AccumP<PS>::value>::type RA;
             const double* sc = A.scal + rhs * A.scal_rs;
             const RA alpha = (RA)((sc[A.s_num] + sc[A.s_num2]) / (sc[A.s_den] + sc[A.s_den2]));
             R pv[24];
             RA xv[24], rv[24];
-            SpinorIO<P>::load(static_cast<const char*>(A.p) + rhs * A.p_rb, A.g.stride, i, pv);
+            SpinorIO<PS>::load(static_cast<const char*>(A.p) + rhs * A.p_rb, A.g.stride, i, pv);
             char* xb = static_cast<char*>(A.x) + rhs * A.acc_rb;
             char* rb = static_cast<char*>(A.r) + rhs * A.acc_rb;
-            SpinorIO<AccumP<P>::value>::load(xb, A.g.stride, i, xv);
-            SpinorIO<AccumP<P>::value>::load(rb, A.g.stride, i, rv);
+            SpinorIO<AccumP<PS>::value>::load(xb, A.g.stride, i, xv);
+            SpinorIO<AccumP<PS>::value>::load(rb, A.g.stride, i, rv);
             RA n = 0;
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
                 n += rv[k] * rv[k];
             }
             nrm = (double)n;
-            SpinorIO<AccumP<P>::value>::store(xb, A.g.stride, i, xv);
-            SpinorIO<AccumP<P>::value>::store(rb, A.g.stride, i, rv);
+            SpinorIO<AccumP<PS>::value>::store(xb, A.g.stride, i, xv);
+            SpinorIO<AccumP<PS>::value>::store(rb, A.g.stride, i, rv);
         } else {
-            SpinorIO<P>::store(static_cast<char*>(A.out) + rhs * A.out_rb, A.g.stride, i, acc);
+            SpinorIO<PS>::store(static_cast<char*>(A.out) + rhs * A.out_rb, A.g.stride, i, acc);
             if (RED) {
                 R n = 0;
 #pragma unroll
@@ -256,29 +256,29 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
 }
 
 // Launch helper: grid (ceil(Vh / block), nrhs).
-template <int P, int RECON, bool DAG, int EPI, bool RED>
+template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
 cudaError_t launch_dslash_t(const DslashArgs& A, int nrhs, int block, cudaStream_t s)
 {
     dim3 grid((A.g.Vh + block - 1) / block, nrhs);
-    dslash_kernel<P, RECON, DAG, EPI, RED><<<grid, block, 0, s>>>(A);
+    dslash_kernel<PG, PS, RECON, DAG, EPI, RED><<<grid, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 
-// Runtime dispatch over (recon, dag, epi, red) for a fixed precision P.
-template <int P>
+// Runtime dispatch over (recon, dag, epi, red) for fixed storage precisions.
+template <int PG, int PS>
 cudaError_t dispatch_dslash_p(const DslashArgs& A, int recon, bool dag, int epi, bool red, int nrhs, int block,
                               cudaStream_t s)
 {
 #define LQ_CASE(RC, DG, EP, RD)                                                              \
     if (recon == RC && dag == DG && epi == EP && red == RD)                                 \
-        return launch_dslash_t<P, RC, DG, EP, RD>(A, nrhs, block, s);
+        return launch_dslash_t<PG, PS, RC, DG, EP, RD>(A, nrhs, block, s);
 #define LQ_EPIS(RC, DG)                  \
     LQ_CASE(RC, DG, EPI_NONE, false)     \
     LQ_CASE(RC, DG, EPI_CLOVINV, false)  \
     LQ_CASE(RC, DG, EPI_XPAY, false)     \
     LQ_CASE(RC, DG, EPI_XPAY, true)      \
     LQ_CASE(RC, DG, EPI_CG, true)
-    if constexpr (P == P64) {
+    if constexpr (PG == P64) {
         LQ_EPIS(18, false)
         LQ_EPIS(18, true)
     } else {

@@ -51,6 +51,8 @@ cudaError_t dslash_dispatch_f64(const DslashArgs&, int, bool, int, bool, int, in
 cudaError_t dslash_dispatch_f32(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_f16(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_bf16(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
+cudaError_t dslash_dispatch_f16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
+cudaError_t dslash_dispatch_bf16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 
 struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 
@@ -95,15 +97,17 @@ struct lqcd_ctx {
     int block;               // threads per block of the dslash kernels
     long dslash_count;
     long launches;           // kernels launched by this context (all kinds)
-    int tuned_block[4][2];   // per precision, dag: tuned block size (0 = default)
+    int tuned_block[lqcd::NMODES][2];  // per precision mode, dag: tuned block size (0 = default)
 
-    size_t field_bytes(int P) const { return lqcd::spinor_field_bytes(P, g.stride); }
+    // bytes of one single-parity spinor field of precision mode m
+    size_t field_bytes(int m) const { return lqcd::spinor_field_bytes(lqcd::mode_ps(m), g.stride); }
     size_t clov_parity_bytes(int P) const { return (size_t)g.stride * lqcd::clover_site_bytes(P); }
     size_t gauge_parity_mu_bytes(int P) const
     {
         return (size_t)g.stride * lqcd::gauge_link_bytes(P, P == lqcd::P64 ? 18 : cfg.recon);
     }
     int recon_of(int P) const { return P == lqcd::P64 ? 18 : cfg.recon; }
+    // does the context hold links and clover for storage precision P (0..3)?
     bool holds(int P) const { return P == lqcd::P64 || (cfg.prec_mask >> P) & 1; }
 };
 

@@ -18,6 +18,8 @@
 // host reads |r|^2 once per block to decide convergence and replacements.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -44,8 +46,9 @@ struct Cg {
 const void* clov_or_null(lqcd_ctx* c, int P, int parity, bool inverse)
 {
     if (c->csw == 0.0) return nullptr;
-    const char* base = static_cast<const char*>(inverse ? c->clovinv[P] : c->clov[P]);
-    return base + parity * c->clov_parity_bytes(P);
+    const int pg = mode_pg(P);
+    const char* base = static_cast<const char*>(inverse ? c->clovinv[pg] : c->clov[pg]);
+    return base + parity * c->clov_parity_bytes(pg);
 }
 
 // One inner CG iteration j of a block: q = K p, x += alpha p, r -= alpha K^dag q
@@ -193,7 +196,7 @@ lqcd_status run_block(Cg& s, int n, bool ru_at_end)
     for (int j = 0; j < n; ++j) {
         LQ_TRY(cg_iteration(s, j));
         if (ru_at_end && j == n - 1) LQ_TRY(reliable_update(s, j + 1));
-        LQ_TRY(blas_cg_p_update(s.c, s.Pv + s.oi, s.Pi, s.RV + s.oa, s.PA, s.R, s.rbi, s.rba, s.nf, rr_slot(j + 1),
+        LQ_TRY(blas_cg_p_update(s.c, s.Pv + s.oi, mode_ps(s.Pi), s.RV + s.oa, s.PA, s.R, s.rbi, s.rba, s.nf, rr_slot(j + 1),
                                 rr_slot(j)));
     }
     LQ_TRY(blas_copy_scalar(s.c, rr_slot(0), rr_slot(n), s.R));
@@ -297,12 +300,12 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
         // r0 = Mhat^dag bhat_o (x0 = 0)
         LQ_TRY(op_schur(c, s.RH + s.fb64, s.BH + s.fb64, s.T2, P64, true, R, s.rb64, s.rb64, -1));
         LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, R, s.rba, s.rb64, 1, rr_slot(0) + 1));
-        LQ_TRY(convert_field(c, s.Pv + s.fbi, s.Pi, s.RV + s.fba, s.PA, R, s.rbi, s.rba, 1, -1));
+        LQ_TRY(convert_field(c, s.Pv + s.fbi, mode_ps(s.Pi), s.RV + s.fba, s.PA, R, s.rbi, s.rba, 1, -1));
     } else {
         LQ_TRY(op_full(c, s.RH, s.B, P64, true, R, s.rb64));
         LQ_TRY(convert_field(c, s.RV, s.PA, s.RH, P64, R, s.rba, s.rb64, 1, rr_slot(0)));
         LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, R, s.rba, s.rb64, 1, rr_slot(0) + 1));
-        LQ_TRY(convert_field(c, s.Pv, s.Pi, s.RV, s.PA, R, s.rbi, s.rba, 2, -1));
+        LQ_TRY(convert_field(c, s.Pv, mode_ps(s.Pi), s.RV, s.PA, R, s.rbi, s.rba, 2, -1));
     }
     std::vector<double> h;
     LQ_TRY(read_scalars(c, R, h));
@@ -322,6 +325,7 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
     const int ru_every = mixed ? p->reliable_interval : 0;
     const double delta2 = p->reliable_delta * p->reliable_delta;
     const bool graphs = p->use_graph && c->stream != nullptr;
+    const bool log = getenv("LQCD_LOG") != nullptr;  // residual history on stderr
     std::vector<BlockGraph> cache;
     int k = 0, since_ru = 0;
     bool ru_next = false;
@@ -390,9 +394,12 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
         for (int r = 0; r < R; ++r) {
             if (done[r]) continue;
             const double rr = h[r * SC_PER_RHS + rr_slot(0)] + h[r * SC_PER_RHS + rr_slot(0) + 1];
+            if (log) fprintf(stderr, "[lqcd] rhs %d iter %d |r|^2/|r0|^2 %.3e%s\n", r, k, rr / rr0[r], ru ? " (reliable update)" : "");
             if (!std::isfinite(rr) || rr > 1e30 * rr0[r]) {
                 for (auto& e : cache) cudaGraphExecDestroy(e.exec);
-                return fail(LQCD_ERR_BREAKDOWN, "lqcd_solve: residual is not finite or diverged");
+                char msg[160];
+                snprintf(msg, sizeof msg, "lqcd_solve: residual not finite or diverged (rhs %d, iteration %d, |r|^2 = %g)", r, k, rr);
+                return fail(LQCD_ERR_BREAKDOWN, msg);
             }
             if (ru) rrmax[r] = rr;
             if (rr > rrmax[r]) rrmax[r] = rr;
@@ -412,6 +419,7 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
                 const double rr = h[r * SC_PER_RHS + rr_slot(0)] + h[r * SC_PER_RHS + rr_slot(0) + 1];
                 if (rr > target[r]) continue;
                 const double res = std::sqrt(h[r * SC_PER_RHS + SC_TMP + 2] / bn2[r]);
+                if (log) fprintf(stderr, "[lqcd] rhs %d iter %d true residual %.3e\n", r, k, res);
                 if (res <= 0.5 * tol) {
                     done[r] = 1;
                     skip[r] = 1;

