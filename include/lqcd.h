@@ -192,6 +192,23 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p);
 lqcd_status lqcd_solve(lqcd_ctx* ctx, double* x, const double* b, double tol, int nrhs,
                        const lqcd_solver_params* params, lqcd_solver_stats* stats);
 
+/* Same result as lqcd_dslash(ctx, out, in, 1, kappa, csw, LQCD_OP_SCHUR |
+ * (dag ? LQCD_DAG : 0), prec, nrhs), but the even-parity intermediate between
+ * the two hopping sweeps lives in a 32 MiB array that the library's CUDA
+ * module carries on every GPU that loads it (held until the process exits),
+ * not in the context's workspace.  For callers that cannot allocate device
+ * memory where they apply the operator.  The paper has no counterpart.
+ *   - The call allocates nothing and calls no allocating routine.
+ *   - Limit: nrhs x lqcd_field_bytes(prec) <= 32 MiB, else LQCD_ERR_INVALID.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls that overlap on the
+ *     GPU (other streams, other contexts, other threads) race.  Nothing in it
+ *     needs clearing: each call overwrites the part it reads.
+ * Inputs and outputs are internal odd-parity fields as for lqcd_dslash. */
+lqcd_status lqcd_dslash_schur_static(lqcd_ctx* ctx, void* out, const void* in, double kappa, double csw,
+                                     int dag, lqcd_prec prec, int nrhs);
+
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 

@@ -81,6 +81,7 @@ _SIGS = {
     "lqcd_sync": [_P],
     "lqcd_profile_enable": [_P, _I],
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
+    "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -199,6 +200,14 @@ def lqcd_unpack(ctx, canonical, internal, parity, prec, nrhs=1):
 def lqcd_dslash(ctx, out, inp, parity, kappa, csw, op_flags, prec, nrhs=1):
     _check(_lib.lqcd_dslash(ctx, _ptr(out), _ptr(inp), int(parity), float(kappa), float(csw),
                             int(op_flags), PREC.get(prec, prec), int(nrhs)), "lqcd_dslash")
+
+
+def lqcd_dslash_schur_static(ctx, out, inp, kappa, csw, dag, prec, nrhs=1):
+    """Schur operator with its intermediate in the library's fixed device
+    array (no workspace scratch); see include/lqcd.h."""
+    _check(_lib.lqcd_dslash_schur_static(ctx, _ptr(out), _ptr(inp), float(kappa), float(csw),
+                                         int(bool(dag)), PREC.get(prec, prec), int(nrhs)),
+           "lqcd_dslash_schur_static")
 
 
 def lqcd_clover_apply(ctx, out, inp, parity, inverse, prec, nrhs=1):
