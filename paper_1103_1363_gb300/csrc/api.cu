@@ -2,6 +2,7 @@
 // gauge and clover set-up, packing, operator application.
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -264,7 +265,11 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     c->g.Vh = (int)(V / 2);
     c->g.stride = (c->g.Vh + 127) / 128 * 128;
     c->g.tanti = cfg->t_antiperiodic ? 1 : 0;
-    c->block = 128;
+    c->block = DSLASH_MAX_BLOCK;
+    if (const char* eb = getenv("LQCD_DSLASH_BLOCK")) {  // experiments: threads per dslash block
+        const int b = atoi(eb);
+        if (b >= 32 && b <= DSLASH_MAX_BLOCK && b % 32 == 0) c->block = b;
+    }
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         c->device = 0;

@@ -171,8 +171,15 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
     accumulate<MU, DAG ? -1 : +1>(acc, w);
 }
 
+// Threads per block are at most DSLASH_MAX_BLOCK; DSLASH_MIN_BLOCKS resident
+// blocks per SM caps the registers so that enough warps are in flight to
+// cover the latency of the neighbour gathers.
+#ifndef LQCD_DSLASH_MINB
+#define LQCD_DSLASH_MINB 5
+#endif
+#define DSLASH_MAX_BLOCK 128
 template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
-__global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A)
+__global__ void __launch_bounds__(DSLASH_MAX_BLOCK, (PG == P64 ? 1 : LQCD_DSLASH_MINB)) dslash_kernel(const DslashArgs A)
 {
     typedef typename RealT<PS>::type R;
     const int rhs = blockIdx.y;

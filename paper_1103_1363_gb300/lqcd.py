@@ -17,7 +17,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblqcd.so")
+# LQCD_LIB selects another build of the same library (kernel experiments)
+LIB_PATH = os.environ.get("LQCD_LIB") or os.path.join(_HERE, "liblqcd.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("liblqcd.so is not built: run __graft_entry__.build() (nvcc, sm_103a)")
