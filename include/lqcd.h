@@ -209,6 +209,55 @@ lqcd_status lqcd_solve(lqcd_ctx* ctx, double* x, const double* b, double tol, in
 lqcd_status lqcd_dslash_schur_static(lqcd_ctx* ctx, void* out, const void* in, double kappa, double csw,
                                      int dag, lqcd_prec prec, int nrhs);
 
+/* ---------------------------------------------------------------------
+ * Learned preconditioner: a gauge-equivariant network of parallel-transport
+ * convolutions, used as the right preconditioner of flexible GCR.  (The
+ * paper preconditions FGCR with SAP and notes that the flexible outer
+ * iteration tolerates a preconditioner that is not a fixed operator, Sec. 5;
+ * the network takes SAP's slot.)  A layer maps C_in to C_out channels of
+ * spinor fields:
+ *   out(x)[co][s] = sum_{h=0..8} sum_{ci,r} W_h[co*4+s][ci*4+r] (T_h in)(x)[ci][r]
+ * T_0 = 1, T_{2mu+1} in(x) = U_mu(x) in(x+mu), T_{2mu+2} in(x) = U_mu(x-mu)^dag in(x-mu),
+ * with the fermion t sign; the links are the context's F32 copy.  The
+ * network is linear (no activation, no bias).
+ * Activations: FP32 complex, [batch][site][channel][spin][colour], canonical
+ * site order; the network's input and output are canonical FP32 spinors.
+ * Weights: FP32 complex, layer after layer, each [9][4 C_out][4 C_in].
+ * Gradients are dL/dRe W + i dL/dIm W.  bf16 = 1 runs the channel
+ * contractions on the tensor cores with BF16 operands and FP32
+ * accumulation; bf16 = 0 runs them in FP32. */
+typedef struct lqcd_net lqcd_net;
+/* channels[0..nlayers], channels[0] = channels[nlayers] = 1, each <= 12;
+ * max_batch: largest batch of forward / training calls.  Needs F32 links. */
+lqcd_status lqcd_net_create(lqcd_ctx* ctx, int nlayers, const int* channels, int bf16, int max_batch,
+                            lqcd_net** out);
+lqcd_status lqcd_net_destroy(lqcd_net* net);
+lqcd_status lqcd_net_workspace_size(const lqcd_net* net, size_t* bytes);
+/* Caller-owned device workspace, 256-byte aligned; weights start at zero. */
+lqcd_status lqcd_net_set_workspace(lqcd_net* net, void* dev_ptr, size_t bytes);
+lqcd_status lqcd_net_num_weights(const lqcd_net* net, size_t* complex_count);
+/* w: host or device FP32 complex weights (resets the Adam moments). */
+lqcd_status lqcd_net_set_weights(lqcd_net* net, const float* w);
+/* Copy the weights and / or the last gradient out (either may be NULL). */
+lqcd_status lqcd_net_get_weights(const lqcd_net* net, float* w, float* grad);
+/* One layer (adjoint = 0) or its adjoint (adjoint = 1, the input gradient:
+ * sum_h T_h^dag W_h^dag applied to `in`) on device activations. */
+lqcd_status lqcd_net_layer_apply(lqcd_net* net, int layer, int adjoint, float* out, const float* in, int batch);
+/* Weight gradient of one layer from its input activations and output
+ * gradient, added into the net's gradient buffer (zeroed first if zero). */
+lqcd_status lqcd_net_layer_wgrad(lqcd_net* net, int layer, const float* in, const float* gout, int batch, int zero);
+/* out = N(in) for batch canonical FP32 spinors (device). */
+lqcd_status lqcd_net_forward(lqcd_net* net, float* out, const float* in, int batch);
+/* One Adam step on L = mean_b |N(r_b) - e_b|^2 / |e_b|^2 over batch pairs of
+ * canonical FP32 spinors (device); *loss (may be NULL) receives L before the
+ * step (reading it synchronises the stream). */
+lqcd_status lqcd_net_train_step(lqcd_net* net, const float* r, const float* e, int batch, double lr, double beta1,
+                                double beta2, double eps, double* loss);
+
+/* Right preconditioner of LQCD_SOLVER_FGCR (NULL: identity, i.e. plain
+ * GCR).  The network must belong to this context and outlive its use. */
+lqcd_status lqcd_set_preconditioner(lqcd_ctx* ctx, lqcd_net* net);
+
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 

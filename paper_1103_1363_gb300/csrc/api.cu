@@ -302,7 +302,8 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     take(c->s_vec64, (size_t)NV64 * R * full64);
     take(c->s_veclo, (size_t)NVLO * R * full64);
     take(c->s_vecacc, (size_t)NVACC * R * full64);
-    c->gcr_bytes = cfg->gcr_nkrylov > 0 ? (size_t)(2 * cfg->gcr_nkrylov + 4) * 2 * c->field_bytes(P32) : 0;
+    // FGCR: z_0..z_{k-1}, w_0..w_{k-1}, r, x (FP32 full fields) + scalars and reduction partials
+    c->gcr_bytes = cfg->gcr_nkrylov > 0 ? (size_t)(2 * cfg->gcr_nkrylov + 2) * 2 * c->field_bytes(P32) + (256 << 10) : 0;
     take(c->s_gcr, c->gcr_bytes);
     c->need = off;
     *out = c;
@@ -590,6 +591,13 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
     if (err & ERRW_BREAKDOWN) return fail(LQCD_ERR_BREAKDOWN, "solver breakdown");
     return LQCD_OK;
     LQ_GUARD_END
+}
+
+lqcd_status lqcd_set_preconditioner(lqcd_ctx* c, lqcd_net* net)
+{
+    if (!c) return fail(LQCD_ERR_INVALID, "null context");
+    c->precond = net;
+    return LQCD_OK;
 }
 
 lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)

@@ -60,6 +60,7 @@ struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 
 struct lqcd_ctx {
     lqcd::Profiler* prof;    // null unless lqcd_profile_enable was called
+    lqcd_net* precond;       // FGCR right preconditioner (null: identity)
     lqcd_config cfg;
     lqcd::Geom g;
     cudaStream_t stream;
@@ -161,5 +162,8 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
 // solver.cu
 lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int nrhs, const lqcd_solver_params* p,
                   lqcd_solver_stats* st);
+// fgcr.cu
+lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, double tol,
+                       const lqcd_solver_params* p, lqcd_solver_stats* st, bool host_io);
 
 }  // namespace lqcd

@@ -237,7 +237,12 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
                   lqcd_solver_stats* st)
 {
     const auto t_start = std::chrono::steady_clock::now();
-    if (p->solver == LQCD_SOLVER_FGCR) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR is not available in this build");
+    if (p->solver == LQCD_SOLVER_FGCR) {
+        if (R != 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR solves one right-hand side per call");
+        const bool hio = !is_device(b);
+        if (hio != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
+        return solve_fgcr(c, c->precond, x, b, tol, p, st, hio);
+    }
     if (p->solver != LQCD_SOLVER_CG_EO && p->solver != LQCD_SOLVER_CG_FULL)
         return fail(LQCD_ERR_INVALID, "lqcd_solve: unknown solver");
     if (p->check_interval < 1 || p->check_interval > SC_RING - 2)

@@ -83,6 +83,18 @@ _SIGS = {
     "lqcd_profile_enable": [_P, _I],
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
+    "lqcd_set_preconditioner": [_P, _P],
+    "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
+    "lqcd_net_destroy": [_P],
+    "lqcd_net_workspace_size": [_P, C.POINTER(_S)],
+    "lqcd_net_set_workspace": [_P, _P, _S],
+    "lqcd_net_num_weights": [_P, C.POINTER(_S)],
+    "lqcd_net_set_weights": [_P, _P],
+    "lqcd_net_get_weights": [_P, _P, _P],
+    "lqcd_net_layer_apply": [_P, _I, _I, _P, _P, _I],
+    "lqcd_net_layer_wgrad": [_P, _I, _P, _P, _I, _I],
+    "lqcd_net_forward": [_P, _P, _P, _I],
+    "lqcd_net_train_step": [_P, _P, _P, _I, _D, _D, _D, _D, C.POINTER(_D)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -256,6 +268,75 @@ def solver_params(**kw):
             v = PREC.get(v, v)
         setattr(p, k, v)
     return p
+
+
+class Net:
+    """A parallel-transport convolution network bound to a Lattice (thin
+    owner of an lqcd_net handle and its workspace tensor)."""
+
+    def __init__(self, lat, channels=(1, 12, 12, 1), bf16=True, max_batch=1):
+        self.lat = lat
+        self.channels = tuple(int(c) for c in channels)
+        arr = (C.c_int * len(self.channels))(*self.channels)
+        h = C.c_void_p()
+        _check(_lib.lqcd_net_create(lat.ctx, len(self.channels) - 1, arr, int(bool(bf16)),
+                                    int(max_batch), C.byref(h)), "lqcd_net_create")
+        self.h = h
+        n = C.c_size_t()
+        _check(_lib.lqcd_net_workspace_size(h, C.byref(n)), "lqcd_net_workspace_size")
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=lat.device)
+        off = (-self.workspace.data_ptr()) % 256
+        _check(_lib.lqcd_net_set_workspace(h, C.c_void_p(self.workspace.data_ptr() + off), n.value),
+               "lqcd_net_set_workspace")
+        _check(_lib.lqcd_net_num_weights(h, C.byref(n)), "lqcd_net_num_weights")
+        self.num_weights = n.value
+
+    def close(self):
+        if self.h is not None:
+            _lib.lqcd_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def use_as_preconditioner(self, enable=True):
+        """Make this network the FGCR right preconditioner of its lattice."""
+        _check(_lib.lqcd_set_preconditioner(self.lat.ctx, self.h if enable else None),
+               "lqcd_set_preconditioner")
+
+    def set_weights(self, w):
+        """w: complex64 tensor/array of num_weights entries."""
+        t = torch.as_tensor(w).to(torch.complex64).contiguous()
+        assert t.numel() == self.num_weights
+        _check(_lib.lqcd_net_set_weights(self.h, _ptr(t)), "lqcd_net_set_weights")
+        torch.cuda.synchronize()
+
+    def get_weights(self, grad=False):
+        w = torch.empty(self.num_weights, dtype=torch.complex64)
+        g = torch.empty(self.num_weights, dtype=torch.complex64) if grad else None
+        _check(_lib.lqcd_net_get_weights(self.h, _ptr(w), _ptr(g) if grad else None),
+               "lqcd_net_get_weights")
+        return (w, g) if grad else w
+
+    def layer_apply(self, layer, out, inp, batch=1, adjoint=False):
+        _check(_lib.lqcd_net_layer_apply(self.h, int(layer), int(bool(adjoint)), _ptr(out), _ptr(inp),
+                                         int(batch)), "lqcd_net_layer_apply")
+
+    def layer_wgrad(self, layer, inp, gout, batch=1, zero=True):
+        _check(_lib.lqcd_net_layer_wgrad(self.h, int(layer), _ptr(inp), _ptr(gout), int(batch),
+                                         int(bool(zero))), "lqcd_net_layer_wgrad")
+
+    def forward(self, out, inp, batch=1):
+        _check(_lib.lqcd_net_forward(self.h, _ptr(out), _ptr(inp), int(batch)), "lqcd_net_forward")
+
+    def train_step(self, r, e, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        loss = C.c_double()
+        _check(_lib.lqcd_net_train_step(self.h, _ptr(r), _ptr(e), int(batch), lr, beta1, beta2, eps,
+                                        C.byref(loss)), "lqcd_net_train_step")
+        return loss.value
 
 
 # --------------------------------------------------------------- convenience

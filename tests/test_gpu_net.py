@@ -1,0 +1,127 @@
+"""GPU parity of the parallel-transport convolution network against the FP64
+oracle: each layer, its adjoint (input gradient) and its weight gradient;
+the whole-network gradient of a training step against oracle backprop.
+
+Tolerances: FP32 path rel-L2 <= 1e-5 (FP32 rounding of sums of ~900
+terms); BF16 tensor-core path <= 2e-2 (8-bit mantissa operands, FP32
+accumulation) and its error is printed."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_helpers import rel, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (4, 4, 6, 8)
+
+
+def rand_w(rng, cout, cin, scale=0.2):
+    return (scale * (rng.standard_normal((9, 4 * cout, 4 * cin))
+                     + 1j * rng.standard_normal((9, 4 * cout, 4 * cin)))).astype(np.complex128)
+
+
+def field(dims, ch, seed, batch=1):
+    f = synth.gaussian_spinor(dims, seed, nfields=batch * ch)
+    lt, lz, ly, lx = dims[3], dims[2], dims[1], dims[0]
+    f = f.reshape(batch, ch, lt, lz, ly, lx, 4, 3)
+    return np.ascontiguousarray(np.moveaxis(f, 1, 5))  # (B, Lt, Lz, Ly, Lx, ch, 4, 3)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).cuda()
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_cuda()
+
+
+def make(lq, channels, bf16, U, max_batch=2):
+    lat = lq.Lattice(DIMS, max_nrhs=1)
+    lat.gauge_load(U)
+    net = lq.Net(lat, channels, bf16=bf16, max_batch=max_batch)
+    return lat, net
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_layers_forward_adjoint_wgrad(lq, bf16):
+    U = synth.smooth_gauge(DIMS, 0.5, 31)
+    rng = np.random.default_rng(0)
+    chans = (1, 12, 12, 1)
+    Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
+    lat, net = make(lq, chans, bf16, U)
+    net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
+    tol = 2e-2 if bf16 else 1e-5
+    B = 2
+    for l in range(3):
+        cin, cout = chans[l], chans[l + 1]
+        x = field(DIMS, cin, 40 + l, B)
+        g = field(DIMS, cout, 50 + l, B)
+        out = torch.empty(x.shape[:5] + (cout, 4, 3), dtype=torch.complex64, device="cuda")
+        net.layer_apply(l, out, dev(x), batch=B)
+        gin = torch.empty(x.shape, dtype=torch.complex64, device="cuda")
+        net.layer_apply(l, gin, dev(g), batch=B, adjoint=True)
+        net.layer_wgrad(l, dev(x), dev(g), batch=B, zero=True)
+        torch.cuda.synchronize()
+        _, grad = net.get_weights(grad=True)
+        off = sum(w.size for w in Ws[:l])
+        gW = grad.numpy()[off:off + Ws[l].size].reshape(Ws[l].shape)
+        want_out = np.stack([oracle.net_layer(U, Ws[l], x[b]) for b in range(B)])
+        want_gin = np.stack([oracle.net_layer_adj(U, Ws[l], g[b]) for b in range(B)])
+        want_gW = sum(oracle.net_layer_wgrad(U, x[b], g[b], cout) for b in range(B))
+        e1, e2 = rel(out.cpu().numpy(), want_out), rel(gin.cpu().numpy(), want_gin)
+        e3 = rel(gW, want_gW)
+        print("layer %d bf16=%d: fwd %.2e adj %.2e wgrad %.2e" % (l, bf16, e1, e2, e3))
+        assert e1 < tol and e2 < tol and e3 < 1e-5
+
+
+def test_train_step_gradient_matches_oracle_backprop(lq):
+    U = synth.smooth_gauge(DIMS, 0.5, 32)
+    rng = np.random.default_rng(1)
+    chans = (1, 4, 3, 1)
+    Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
+    lat, net = make(lq, chans, False, U, max_batch=2)
+    net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
+    B = 2
+    r = field(DIMS, 1, 60, B)
+    e = field(DIMS, 1, 61, B)
+    rs = r[:, :, :, :, :, 0]
+    es = e[:, :, :, :, :, 0]
+    loss = net.train_step(dev(rs), dev(es), B, lr=0.0)
+    torch.cuda.synchronize()
+    _, grad = net.get_weights(grad=True)
+    # oracle: forward, loss, backprop
+    acts = [r]
+    for l in range(3):
+        acts.append(np.stack([oracle.net_layer(U, Ws[l], acts[-1][b]) for b in range(B)]))
+    y = acts[-1]
+    en2 = np.array([np.sum(np.abs(e[b]) ** 2) for b in range(B)])
+    want_loss = np.mean([np.sum(np.abs(y[b] - e[b]) ** 2) / en2[b] for b in range(B)])
+    assert abs(loss - want_loss) / want_loss < 1e-5
+    g = np.stack([2 * (y[b] - e[b]) / (B * en2[b]) for b in range(B)])
+    want = []
+    for l in range(2, -1, -1):
+        want.insert(0, sum(oracle.net_layer_wgrad(U, acts[l][b], g[b], chans[l + 1]) for b in range(B)))
+        g = np.stack([oracle.net_layer_adj(U, Ws[l], g[b]) for b in range(B)])
+    want = np.concatenate([w.reshape(-1) for w in want])
+    err = rel(grad.numpy(), want)
+    print("train-step gradient rel err %.2e" % err)
+    assert err < 1e-5
+
+
+def test_training_reduces_loss(lq):
+    U = synth.smooth_gauge(DIMS, 0.5, 33)
+    lat, net = make(lq, (1, 4, 1), True, U, max_batch=4)
+    rng = np.random.default_rng(2)
+    net.set_weights(np.concatenate([rand_w(rng, 4, 1, 0.1).reshape(-1), rand_w(rng, 1, 4, 0.1).reshape(-1)]))
+    # targets made by a fixed random linear map of the same form: learnable exactly
+    Wt = [rand_w(rng, 4, 1, 0.3), rand_w(rng, 1, 4, 0.3)]
+    r = field(DIMS, 1, 70, 4)
+    e = np.stack([oracle.net_layer(U, Wt[1], oracle.net_layer(U, Wt[0], r[b])) for b in range(4)])
+    rd, ed = dev(r[..., 0, :, :]), dev(e[..., 0, :, :])
+    losses = [net.train_step(rd, ed, 4, lr=2e-2) for _ in range(150)]
+    print("loss %.3e -> %.3e" % (losses[0], losses[-1]))
+    assert losses[-1] < 0.05 * losses[0]
