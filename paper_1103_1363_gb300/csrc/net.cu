@@ -460,7 +460,7 @@ struct lqcd_net {
     float* act[9];         // activations per layer boundary: [max_batch][V][ch][4][3] complex
     float* gact[2];        // gradient ping-pong buffers (max channels)
     double* red;           // loss reductions [max_batch][2]
-    double* partials;      // loss reduction partials [max_batch][NET_PARTIALS]
+    double* partials;      // loss reduction partials [max_batch][NET_PARTIALS][2]
     unsigned* tickets;     // [max_batch]
     size_t woff[9];        // float offsets of layer weights in W (layer nlayers = total)
     size_t boff[8], bhoff[8];
@@ -614,7 +614,7 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
         size_t oG0 = take((size_t)max_batch * act_floats(n, cmax) * 4);
         size_t oG1 = take((size_t)max_batch * act_floats(n, cmax) * 4);
         size_t oR = take((size_t)max_batch * 2 * sizeof(double));
-        size_t oP = take((size_t)max_batch * NET_PARTIALS * sizeof(double));
+        size_t oP = take((size_t)max_batch * 2 * NET_PARTIALS * sizeof(double));  // 2 sums per block
         size_t oT = take((size_t)max_batch * sizeof(unsigned));
         n->need = off;
         // stash offsets in the pointer fields until the workspace arrives
@@ -769,7 +769,7 @@ lqcd_status lqcd_net_train_step(lqcd_net* n, const float* r, const float* e, int
     // loss and its gradient
     const int nb = 256;
     dim3 g1(NET_PARTIALS, batch);
-    net_loss_reduce_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], e, n_per, n->partials, NET_PARTIALS,
+    net_loss_reduce_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], e, n_per, n->partials, 2 * NET_PARTIALS,
                                                      n->tickets, n->red);
     LQ_CUDA(cudaGetLastError());
     net_loss_grad_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], e, n_per, n->red, batch, n->gact[0]);

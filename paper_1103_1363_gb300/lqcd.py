@@ -359,6 +359,8 @@ class Lattice:
             self._ws_view = self.workspace[off:off + n]
             lqcd_set_workspace(self.ctx, self._ws_view)
         self.volume = int(np.prod(self.dims))
+        self.max_nrhs = int(max_nrhs)
+        self.kappa, self.csw = 0.0, 0.0
 
     def close(self):
         if self.ctx is not None:
@@ -391,6 +393,7 @@ class Lattice:
 
     def clover_compute(self, kappa, csw):
         lqcd_clover_compute(self.ctx, kappa, csw)
+        self.kappa, self.csw = float(kappa), float(csw)
 
     def pack(self, internal, canonical, parity, prec, nrhs=1):
         lqcd_pack(self.ctx, internal, _as_tensor(canonical, self.device), parity, prec, nrhs)

@@ -53,8 +53,28 @@ def test_fgcr_identity_and_hopping_preconditioner(lq):
     net.use_as_preconditioner(False)
 
 
+def hopping_net_weights(kappa, chans, rng, noise):
+    """Weights of a (1, C, C, 1) network that computes 1 + kappa H through
+    channel 0 (identity in the first layers, the hopping expansion in the
+    last), plus small random weights everywhere."""
+    ws = []
+    for l in range(3):
+        cin, cout = chans[l], chans[l + 1]
+        w = noise * (rng.standard_normal((9, 4 * cout, 4 * cin)) + 1j * rng.standard_normal((9, 4 * cout, 4 * cin)))
+        w[0, :4, :4] += np.eye(4)
+        if l == 2:
+            for mu in range(4):
+                g = oracle.gamma(mu)
+                w[2 * mu + 1, :4, :4] += kappa * (np.eye(4) - g)
+                w[2 * mu + 2, :4, :4] += kappa * (np.eye(4) + g)
+        ws.append(w.reshape(-1))
+    return np.concatenate(ws)
+
+
 @pytest.mark.parametrize("bf16", [False, True])
-def test_fgcr_clover_random_net(lq, bf16):
+def test_fgcr_clover_three_layer_net(lq, bf16):
+    """A (1, 12, 12, 1) network near 1 + kappa H (perturbed by noise) in the
+    FGCR slot, FP32 and BF16 tensor-core layers, with clover."""
     dims = (8, 8, 8, 8)
     kappa, csw = 0.13, 1.0
     U = synth.smooth_gauge(dims, 0.5, 42)
@@ -62,12 +82,13 @@ def test_fgcr_clover_random_net(lq, bf16):
     lat = lq.Lattice(dims, gcr_nkrylov=20)
     lat.gauge_load(U)
     lat.clover_compute(kappa, csw)
+    _, st_id = solve(lq, lat, b)
     net = lq.Net(lat, (1, 12, 12, 1), bf16=bf16)
-    rng = np.random.default_rng(3)
-    w = 0.05 * (rng.standard_normal(net.num_weights) + 1j * rng.standard_normal(net.num_weights))
-    net.set_weights(w)
+    net.set_weights(hopping_net_weights(kappa, (1, 12, 12, 1), np.random.default_rng(3), 0.002))
     net.use_as_preconditioner()
     x, st = solve(lq, lat, b)
     res = oracle.true_residual(U, oracle.clover(U, kappa, csw), kappa, b, x)
-    print("fgcr random net bf16=%d: %d iters, res %.2e" % (bf16, st["iterations"], res))
+    print("fgcr 3-layer net bf16=%d: %d iters (identity %d), res %.2e" % (
+        bf16, st["iterations"], st_id["iterations"], res))
     assert res <= 1e-10
+    assert st["iterations"] < st_id["iterations"]
