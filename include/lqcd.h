@@ -177,6 +177,9 @@ typedef struct {
     long kernel_launches;    /* kernels launched by the call (graph replays count their nodes) */
     double true_residual;    /* |b - M x| / |b| in FP64 on the device (max over rhs) */
     double seconds;          /* wall time of the call */
+    int preconditioner_fallback; /* FGCR: 1 if the preconditioner stagnated (a restart
+                                    cycle did not halve the residual) and the solve
+                                    finished with the identity */
 } lqcd_solver_stats;
 
 /* Defaults: CG_EO, F32 inner, maxiter 100000, reliable every 50, delta 0.1,

@@ -204,8 +204,8 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     const double bn2 = h[SC_TMP + 0];
     const int block = 256;
     const dim3 grid(gcr_grid(c, block));
-    int iters = 0, restarts = 0;
-    double res = 1.0;
+    int iters = 0, restarts = 0, fallback = 0;
+    double res = 1.0, res_prev = 0.0;
     lqcd_status status = LQCD_OK;
     while (true) {
         // restart: r = b - M x in FP64; stop on the true residual
@@ -216,6 +216,14 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         if (log) fprintf(stderr, "[lqcd] fgcr iter %d restart, true residual %.3e\n", iters, res);
         if (!std::isfinite(res)) { status = LQCD_ERR_BREAKDOWN; break; }
         if (res <= tol) break;
+        // safeguard: a preconditioner that does not halve the residual over a
+        // whole cycle is replaced by the identity for the rest of the solve
+        if (net && restarts > 0 && res > 0.5 * res_prev) {
+            net = nullptr;
+            fallback = 1;
+            if (log) fprintf(stderr, "[lqcd] fgcr: preconditioner stagnates, continuing with the identity\n");
+        }
+        res_prev = res;
         if (iters >= p->maxiter) { status = LQCD_ERR_NOT_CONVERGED; break; }
         restarts++;
         LQ_TRY(convert_field(c, R32, P32, T2, P64, 1, fld, rb64, 2, -1));
@@ -259,6 +267,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     st->dslash_count = c->dslash_count;
     st->kernel_launches = c->launches;
     st->true_residual = res;
+    st->preconditioner_fallback = fallback;
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (status == LQCD_ERR_NOT_CONVERGED) return fail(status, "lqcd_solve: FGCR not converged within maxiter");
     if (status == LQCD_ERR_BREAKDOWN) return fail(status, "lqcd_solve: FGCR breakdown");

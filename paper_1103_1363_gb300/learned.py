@@ -47,16 +47,24 @@ def apply_full_operator(lat, out_canon, in_canon, nrhs):
     lat.unpack(out_canon, f_out, -1, "f64", nrhs=nrhs)
 
 
-def make_pairs(lat, npairs, seed, cg_iters=20, chunk=None):
-    """(r, e) as complex64 device tensors of shape (npairs, Lt, Lz, Ly, Lx, 4, 3)."""
+def make_pairs(lat, npairs, seed, cg_iters=20, with_start=True, chunk=None):
+    """(r, e) as complex64 device tensors of shape (npairs, Lt, Lz, Ly, Lx, 4, 3).
+
+    Each CG run gives its pair after cg_iters iterations and, when
+    with_start, also its pair at iteration 0, (b, x*): the 20-iteration
+    residuals carry almost no high-mode content, and a network trained on
+    them alone learns nothing about the high modes of a Gaussian source.
+    With with_start, npairs // 2 runs are made (npairs even)."""
     chunk = chunk or lat.max_nrhs
     lx, ly, lz, lt = lat.dims
     shape = (lt, lz, ly, lx, 4, 3)
     R = torch.empty((npairs,) + shape, dtype=torch.complex64, device=lat.device)
     E = torch.empty_like(R)
+    runs = npairs // 2 if with_start else npairs
     gen = torch.Generator(device="cpu").manual_seed(int(seed))
-    for p0 in range(0, npairs, chunk):
-        n = min(chunk, npairs - p0)
+    k = 0
+    for p0 in range(0, runs, chunk):
+        n = min(chunk, runs - p0)
         xs = (torch.randn((n,) + shape, dtype=torch.complex128, generator=gen)).to(lat.device)
         b = torch.empty_like(xs)
         apply_full_operator(lat, b, xs, n)
@@ -65,10 +73,15 @@ def make_pairs(lat, npairs, seed, cg_iters=20, chunk=None):
                   maxiter=cg_iters, check_interval=10, reliable_interval=0)
         mx = torch.empty_like(xs)
         apply_full_operator(lat, mx, x20, n)
-        R[p0:p0 + n] = (b - mx).to(torch.complex64)
-        E[p0:p0 + n] = (xs - x20).to(torch.complex64)
+        R[k:k + n] = (b - mx).to(torch.complex64)
+        E[k:k + n] = (xs - x20).to(torch.complex64)
+        k += n
+        if with_start:
+            R[k:k + n] = b.to(torch.complex64)
+            E[k:k + n] = xs.to(torch.complex64)
+            k += n
     torch.cuda.synchronize(lat.device)
-    return R, E
+    return R[:k], E[:k]
 
 
 def train(net, fields, epochs, batch, lr=1e-3, seed=0, log=None):
