@@ -261,6 +261,16 @@ lqcd_status lqcd_net_train_step(lqcd_net* net, const float* r, const float* e, i
  * GCR).  The network must belong to this context and outlive its use. */
 lqcd_status lqcd_set_preconditioner(lqcd_ctx* ctx, lqcd_net* net);
 
+/* Solve the systems of n contexts (lattices of any sizes, one right-hand
+ * side each, canonical FP64 x[i], b[i] on host or device) together with a
+ * CG solver: set-up per lattice, then iteration blocks in lockstep on the
+ * stream of ctxs[0] (every context uses it during the call); with
+ * params->use_graph one CUDA graph holds the block of every lattice still
+ * iterating and is replayed.  Each lattice stops on its own true residual
+ * tol[i] (stats[i]).  Returns the first non-OK status of the lattices. */
+lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b,
+                             const double* tol, const lqcd_solver_params* params, lqcd_solver_stats* stats);
+
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 

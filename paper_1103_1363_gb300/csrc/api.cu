@@ -593,6 +593,28 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
     LQ_GUARD_END
 }
 
+lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b,
+                             const double* tol, const lqcd_solver_params* params, lqcd_solver_stats* stats)
+{
+    LQ_GUARD_BEGIN
+    if (!ctxs || !x || !b || !tol || !stats || n < 1) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: bad argument");
+    lqcd_solver_params p;
+    if (params) p = *params;
+    else lqcd_solver_params_default(&p);
+    for (int i = 0; i < n; ++i) {
+        lqcd_ctx* c = ctxs[i];
+        LQ_TRY(check_ready(c));
+        if (!x[i] || !b[i] || !(tol[i] > 0.0)) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: bad vector or tol");
+        if (!c->gauge_loaded || !c->clover_state) return fail(LQCD_ERR_STATE, "lqcd_solve_batch: gauge and clover first");
+        if (c->device != ctxs[0]->device) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: contexts on different GPUs");
+        LQ_TRY(check_prec(c, p.inner_prec));
+        memset(&stats[i], 0, sizeof(stats[i]));
+    }
+    LQ_TRY(set_device_of(ctxs[0]));
+    return solve_batch(ctxs, n, x, b, tol, &p, stats);
+    LQ_GUARD_END
+}
+
 lqcd_status lqcd_set_preconditioner(lqcd_ctx* c, lqcd_net* net)
 {
     if (!c) return fail(LQCD_ERR_INVALID, "null context");

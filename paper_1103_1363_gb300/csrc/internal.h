@@ -162,6 +162,8 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
 // solver.cu
 lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int nrhs, const lqcd_solver_params* p,
                   lqcd_solver_stats* st);
+lqcd_status solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b, const double* tol,
+                        const lqcd_solver_params* p, lqcd_solver_stats* st);
 // fgcr.cu
 lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, double tol,
                        const lqcd_solver_params* p, lqcd_solver_stats* st, bool host_io);

@@ -222,27 +222,47 @@ bool is_device(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// A captured iteration block (graph), keyed by (length, reliable update).
+// A captured iteration block (graph) for a set of runs, keyed by
+// (length, reliable update, which runs are active).
 struct BlockGraph {
     int n = -1;
     bool ru = false;
+    unsigned long long mask = 0;
     cudaGraphExec_t exec = nullptr;
-    long launches = 0;  // kernel nodes in the graph
-    long dslash = 0;    // hopping applications in the graph
+    std::vector<long> launches;  // kernel nodes per run
+    std::vector<long> dslash;    // hopping applications per run
 };
 
-}  // namespace
-
-lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, const lqcd_solver_params* p,
-                  lqcd_solver_stats* st)
-{
-    const auto t_start = std::chrono::steady_clock::now();
-    if (p->solver == LQCD_SOLVER_FGCR) {
-        if (R != 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR solves one right-hand side per call");
-        const bool hio = !is_device(b);
-        if (hio != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
-        return solve_fgcr(c, c->precond, x, b, tol, p, st, hio);
+// State of one CG solve (one lattice, nrhs right-hand sides).
+struct CgRun {
+    Cg s;
+    lqcd_ctx* c = nullptr;
+    double* x = nullptr;
+    const double* b = nullptr;
+    double tol = 0.0;
+    bool host_io = false;
+    int maxiter = 0;
+    std::vector<double> h, bn2, rr0, target, rrmax;
+    std::vector<int> done;
+    bool mixed = false, log = false, ru_next = false;
+    int ru_every = 0;
+    double delta2 = 0.0;
+    int k = 0, since_ru = 0, nrestart = 0;
+    lqcd_status status = LQCD_OK;
+    std::chrono::steady_clock::time_point t_start;
+    bool finished() const
+    {
+        if (status != LQCD_OK) return true;
+        for (int d : done)
+            if (!d) return false;
+        return true;
     }
+};
+
+lqcd_status cg_setup(CgRun& run, lqcd_ctx* c, double* x, const double* b, double tol, int R,
+                     const lqcd_solver_params* p)
+{
+    run.t_start = std::chrono::steady_clock::now();
     if (p->solver != LQCD_SOLVER_CG_EO && p->solver != LQCD_SOLVER_CG_FULL)
         return fail(LQCD_ERR_INVALID, "lqcd_solve: unknown solver");
     if (p->check_interval < 1 || p->check_interval > SC_RING - 2)
@@ -250,7 +270,12 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
     if (p->maxiter < 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: maxiter must be >= 1");
     c->dslash_count = 0;
     c->launches = 0;
-    Cg s;
+    run.c = c;
+    run.x = x;
+    run.b = b;
+    run.tol = tol;
+    run.maxiter = p->maxiter;
+    Cg& s = run.s;
     s.c = c;
     s.R = R;
     s.Pi = p->inner_prec;
@@ -277,13 +302,13 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
     s.oi = s.eo ? s.fbi : 0;
     s.oa = s.eo ? s.fba : 0;
     const size_t canon_rb = (size_t)c->volume * 192;
-    const bool host_io = !is_device(b);
-    if (host_io != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
-    if (host_io && c->staging_bytes < (size_t)R * canon_rb) return fail(LQCD_ERR_NOMEM, "lqcd_solve: staging too small");
+    run.host_io = !is_device(b);
+    if (run.host_io != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
+    if (run.host_io && c->staging_bytes < (size_t)R * canon_rb) return fail(LQCD_ERR_NOMEM, "lqcd_solve: staging too small");
 
-    // ---- set-up: pack b, scalars to zero
+    // pack b, scalars to zero
     const double* bdev = b;
-    if (host_io) {
+    if (run.host_io) {
         LQ_CUDA(cudaMemcpyAsync(c->staging, b, (size_t)R * canon_rb, cudaMemcpyHostToDevice, c->stream));
         bdev = static_cast<const double*>(c->staging);
     }
@@ -312,138 +337,103 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
         LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, R, s.rba, s.rb64, 1, rr_slot(0) + 1));
         LQ_TRY(convert_field(c, s.Pv, mode_ps(s.Pi), s.RV, s.PA, R, s.rbi, s.rba, 2, -1));
     }
-    std::vector<double> h;
-    LQ_TRY(read_scalars(c, R, h));
-    std::vector<double> bn2(R), rr0(R), target(R), rrmax(R);
-    std::vector<int> done(R, 0);
-    double worst_res = 0.0;
+    LQ_TRY(read_scalars(c, R, run.h));
+    run.bn2.assign(R, 0.0);
+    run.rr0.assign(R, 0.0);
+    run.target.assign(R, 0.0);
+    run.rrmax.assign(R, 0.0);
+    run.done.assign(R, 0);
     for (int r = 0; r < R; ++r) {
-        bn2[r] = h[r * SC_PER_RHS + SC_TMP + 0];
-        rr0[r] = h[r * SC_PER_RHS + rr_slot(0)] + h[r * SC_PER_RHS + rr_slot(0) + 1];
-        target[r] = rr0[r] * tol * tol;
-        rrmax[r] = rr0[r];
-        if (bn2[r] == 0.0 || rr0[r] == 0.0) done[r] = 1;  // b = 0 (x = 0) or exact already
+        run.bn2[r] = run.h[r * SC_PER_RHS + SC_TMP + 0];
+        run.rr0[r] = run.h[r * SC_PER_RHS + rr_slot(0)] + run.h[r * SC_PER_RHS + rr_slot(0) + 1];
+        run.target[r] = run.rr0[r] * tol * tol;
+        run.rrmax[r] = run.rr0[r];
+        if (run.bn2[r] == 0.0 || run.rr0[r] == 0.0) run.done[r] = 1;  // b = 0 (x = 0) or exact already
     }
+    run.mixed = s.Pi != P64;
+    run.ru_every = run.mixed ? p->reliable_interval : 0;
+    run.delta2 = p->reliable_delta * p->reliable_delta;
+    run.log = getenv("LQCD_LOG") != nullptr;  // residual history on stderr
+    return LQCD_OK;
+}
 
-    // ---- iterate in blocks
-    const bool mixed = s.Pi != P64;
-    const int ru_every = mixed ? p->reliable_interval : 0;
-    const double delta2 = p->reliable_delta * p->reliable_delta;
-    const bool graphs = p->use_graph && c->stream != nullptr;
-    const bool log = getenv("LQCD_LOG") != nullptr;  // residual history on stderr
-    std::vector<BlockGraph> cache;
-    int k = 0, since_ru = 0;
-    bool ru_next = false;
-    lqcd_status status = LQCD_OK;
-    int nrestart = 0;
-    while (true) {
-        int ndone = 0;
-        for (int r = 0; r < R; ++r) ndone += done[r];
-        if (ndone == R) break;
-        if (k >= p->maxiter) {
-            status = LQCD_ERR_NOT_CONVERGED;
-            break;
+// After a block of n iterations: read |r|^2, detect breakdown, check
+// candidates on the FP64 true residual, mark converged right-hand sides.
+lqcd_status cg_check(CgRun& run, int n, bool ru)
+{
+    lqcd_ctx* c = run.c;
+    Cg& s = run.s;
+    const int R = s.R;
+    if (ru) {
+        s.reliable++;
+        run.since_ru = 0;
+    } else {
+        run.since_ru += n;
+    }
+    run.k += n;
+    LQ_TRY(read_scalars(c, R, run.h));
+    bool any_candidate = false;
+    for (int r = 0; r < R; ++r) {
+        if (run.done[r]) continue;
+        const double rr = run.h[r * SC_PER_RHS + rr_slot(0)] + run.h[r * SC_PER_RHS + rr_slot(0) + 1];
+        if (run.log)
+            fprintf(stderr, "[lqcd] rhs %d iter %d |r|^2/|r0|^2 %.3e%s\n", r, run.k, rr / run.rr0[r],
+                    ru ? " (reliable update)" : "");
+        if (!std::isfinite(rr) || rr > 1e30 * run.rr0[r]) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "lqcd_solve: residual not finite or diverged (rhs %d, iteration %d, |r|^2 = %g)",
+                     r, run.k, rr);
+            run.status = fail(LQCD_ERR_BREAKDOWN, msg);
+            return run.status;
         }
-        int n = p->check_interval;
-        if (n > p->maxiter - k) n = p->maxiter - k;
-        bool ru = false;
-        if (ru_every > 0 && since_ru + n >= ru_every) {
-            n = ru_every - since_ru;
-            if (n < 1) n = 1;
-            ru = true;
+        if (ru) run.rrmax[r] = rr;
+        if (rr > run.rrmax[r]) run.rrmax[r] = rr;
+        if (run.mixed && rr < run.delta2 * run.rrmax[r]) run.ru_next = true;
+        if (rr <= run.target[r]) any_candidate = true;
+    }
+    if (!any_candidate) return LQCD_OK;
+    // true residual of the full system for every rhs (x is folded, r untouched)
+    LQ_TRY(fold_x(s));
+    LQ_TRY(true_system_residual(s));
+    LQ_TRY(read_scalars(c, R, run.h));
+    s.checks++;
+    run.nrestart++;
+    std::vector<int> skip(R, 0);
+    for (int r = 0; r < R; ++r) {
+        if (run.done[r]) {
+            skip[r] = 1;
+            continue;
         }
-        if (ru_next && mixed) {
-            ru = true;
-            ru_next = false;
-        }
-        if (graphs) {
-            BlockGraph* gph = nullptr;
-            for (auto& e : cache)
-                if (e.n == n && e.ru == ru) gph = &e;
-            if (!gph) {
-                cudaGraph_t graph;
-                LQ_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-                const long saved = c->dslash_count, saved_l = c->launches;
-                lqcd_status cs = run_block(s, n, ru);
-                cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
-                BlockGraph e;
-                e.dslash = c->dslash_count - saved;
-                e.launches = c->launches - saved_l;
-                c->dslash_count = saved;
-                c->launches = saved_l;
-                if (cs != LQCD_OK) return cs;
-                LQ_CUDA(ce);
-                e.n = n;
-                e.ru = ru;
-                cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
-                cudaGraphDestroy(graph);
-                LQ_CUDA(ie);
-                cache.push_back(e);
-                gph = &cache.back();
-            }
-            LQ_CUDA(cudaGraphLaunch(gph->exec, c->stream));
-            c->dslash_count += gph->dslash;
-            c->launches += gph->launches;
+        const double rr = run.h[r * SC_PER_RHS + rr_slot(0)] + run.h[r * SC_PER_RHS + rr_slot(0) + 1];
+        if (rr > run.target[r]) continue;
+        const double res = std::sqrt(run.h[r * SC_PER_RHS + SC_TMP + 2] / run.bn2[r]);
+        if (run.log) fprintf(stderr, "[lqcd] rhs %d iter %d true residual %.3e\n", r, run.k, res);
+        if (res <= 0.5 * run.tol) {
+            run.done[r] = 1;
+            skip[r] = 1;
         } else {
-            LQ_TRY(run_block(s, n, ru));
-        }
-        if (ru) {
-            s.reliable++;
-            since_ru = 0;
-        } else {
-            since_ru += n;
-        }
-        k += n;
-        LQ_TRY(read_scalars(c, R, h));
-        bool any_candidate = false;
-        for (int r = 0; r < R; ++r) {
-            if (done[r]) continue;
-            const double rr = h[r * SC_PER_RHS + rr_slot(0)] + h[r * SC_PER_RHS + rr_slot(0) + 1];
-            if (log) fprintf(stderr, "[lqcd] rhs %d iter %d |r|^2/|r0|^2 %.3e%s\n", r, k, rr / rr0[r], ru ? " (reliable update)" : "");
-            if (!std::isfinite(rr) || rr > 1e30 * rr0[r]) {
-                for (auto& e : cache) cudaGraphExecDestroy(e.exec);
-                char msg[160];
-                snprintf(msg, sizeof msg, "lqcd_solve: residual not finite or diverged (rhs %d, iteration %d, |r|^2 = %g)", r, k, rr);
-                return fail(LQCD_ERR_BREAKDOWN, msg);
-            }
-            if (ru) rrmax[r] = rr;
-            if (rr > rrmax[r]) rrmax[r] = rr;
-            if (mixed && rr < delta2 * rrmax[r]) ru_next = true;
-            if (rr <= target[r]) any_candidate = true;
-        }
-        if (any_candidate) {
-            // true residual of the full system for every rhs (x is folded, r untouched)
-            LQ_TRY(fold_x(s));
-            LQ_TRY(true_system_residual(s));
-            LQ_TRY(read_scalars(c, R, h));
-            s.checks++;
-            nrestart++;
-            std::vector<int> skip(R, 0);
-            for (int r = 0; r < R; ++r) {
-                if (done[r]) { skip[r] = 1; continue; }
-                const double rr = h[r * SC_PER_RHS + rr_slot(0)] + h[r * SC_PER_RHS + rr_slot(0) + 1];
-                if (rr > target[r]) continue;
-                const double res = std::sqrt(h[r * SC_PER_RHS + SC_TMP + 2] / bn2[r]);
-                if (log) fprintf(stderr, "[lqcd] rhs %d iter %d true residual %.3e\n", r, k, res);
-                if (res <= 0.5 * tol) {
-                    done[r] = 1;
-                    skip[r] = 1;
-                } else {
-                    double f = (0.25 * tol / res);
-                    f *= f;
-                    if (f > 0.5) f = 0.5;
-                    if (f < 1e-6) f = 1e-6;
-                    target[r] = rr * f;
-                    if (mixed) ru_next = true;
-                }
-            }
-            LQ_CUDA(cudaMemcpyAsync(c->skip, skip.data(), R * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-            LQ_CUDA(cudaStreamSynchronize(c->stream));
+            double f = (0.25 * run.tol / res);
+            f *= f;
+            if (f > 0.5) f = 0.5;
+            if (f < 1e-6) f = 1e-6;
+            run.target[r] = rr * f;
+            if (run.mixed) run.ru_next = true;
         }
     }
-    for (auto& e : cache) cudaGraphExecDestroy(e.exec);
+    LQ_CUDA(cudaMemcpyAsync(c->skip, skip.data(), R * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LQ_CUDA(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
 
-    // ---- finish: fold x, reconstruct x_e, FP64 true residual, unpack
+// Fold x, reconstruct x_e, FP64 true residual, unpack, stats.
+lqcd_status cg_finish(CgRun& run, lqcd_solver_stats* st)
+{
+    lqcd_ctx* c = run.c;
+    Cg& s = run.s;
+    const int R = s.R;
+    const size_t canon_rb = (size_t)c->volume * 192;
+    lqcd_status status = run.status;
+    if (status == LQCD_OK && !run.finished()) status = LQCD_ERR_NOT_CONVERGED;
     LQ_TRY(fold_x(s));
     if (s.eo) {
         // x_e = A_ee^{-1} (b_e + kappa H_eo x_o)
@@ -456,26 +446,176 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, co
     }
     LQ_TRY(op_full(c, s.T1, s.X, P64, false, R, s.rb64));
     LQ_TRY(blas_xmy_norm(c, s.T2, s.B, s.T1, P64, R, s.rb64, 2, SC_TMP + 3));
-    double* xdev = host_io ? static_cast<double*>(c->staging) : x;
+    double* xdev = run.host_io ? static_cast<double*>(c->staging) : run.x;
     LQ_TRY(unpack_spinor(c, xdev, s.X, -1, P64, R, s.rb64, canon_rb));
-    if (host_io) LQ_CUDA(cudaMemcpyAsync(x, c->staging, (size_t)R * canon_rb, cudaMemcpyDeviceToHost, c->stream));
-    LQ_TRY(read_scalars(c, R, h));
+    if (run.host_io)
+        LQ_CUDA(cudaMemcpyAsync(run.x, c->staging, (size_t)R * canon_rb, cudaMemcpyDeviceToHost, c->stream));
+    LQ_TRY(read_scalars(c, R, run.h));
+    double worst = 0.0;
     for (int r = 0; r < R; ++r) {
-        const double res = bn2[r] > 0 ? std::sqrt(h[r * SC_PER_RHS + SC_TMP + 3] / bn2[r]) : 0.0;
-        if (res > worst_res) worst_res = res;
+        const double res = run.bn2[r] > 0 ? std::sqrt(run.h[r * SC_PER_RHS + SC_TMP + 3] / run.bn2[r]) : 0.0;
+        if (res > worst || !std::isfinite(res)) worst = res;
         if (!std::isfinite(res)) status = LQCD_ERR_BREAKDOWN;
-        else if (res > tol && status == LQCD_OK) status = LQCD_ERR_NOT_CONVERGED;
+        else if (res > run.tol && status == LQCD_OK) status = LQCD_ERR_NOT_CONVERGED;
     }
-    st->iterations = k;
+    st->iterations = run.k;
     st->reliable_updates = (int)s.reliable;
-    st->restarts = nrestart;
+    st->restarts = run.nrestart;
     st->dslash_count = c->dslash_count;
     st->kernel_launches = c->launches;
-    st->true_residual = worst_res;
-    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    st->true_residual = worst;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - run.t_start).count();
     if (status == LQCD_ERR_NOT_CONVERGED) return fail(status, "lqcd_solve: not converged within maxiter");
     if (status == LQCD_ERR_BREAKDOWN) return fail(status, "lqcd_solve: breakdown");
     return LQCD_OK;
+}
+
+void destroy_graphs(std::vector<BlockGraph>& cache)
+{
+    for (auto& e : cache)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    cache.clear();
+}
+
+// Iterate every unfinished run in lockstep blocks until all finish or hit
+// maxiter; with graphs, one graph holds the block of every active run.
+lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
+{
+    lqcd_ctx* c0 = runs[0]->c;
+    const bool graphs = p->use_graph && c0->stream != nullptr;
+    std::vector<BlockGraph> cache;
+    while (true) {
+        unsigned long long mask = 0;
+        int kmax = 0, since = 0, ru_every = 0;
+        bool ru_next = false;
+        for (size_t i = 0; i < runs.size(); ++i) {
+            CgRun& r = *runs[i];
+            if (r.finished() || r.k >= r.maxiter) continue;
+            mask |= 1ull << i;
+            kmax = r.k > kmax ? r.k : kmax;
+            since = r.since_ru;
+            ru_every = r.ru_every;
+            ru_next = ru_next || (r.ru_next && r.mixed);
+        }
+        if (!mask) break;
+        int maxiter = p->maxiter;
+        int n = p->check_interval;
+        if (n > maxiter - kmax) n = maxiter - kmax;
+        if (n < 1) break;
+        bool ru = false;
+        if (ru_every > 0 && since + n >= ru_every) {
+            n = ru_every - since;
+            if (n < 1) n = 1;
+            ru = true;
+        }
+        if (ru_next) ru = true;
+        for (auto* r : runs) r->ru_next = false;
+        if (graphs) {
+            BlockGraph* gph = nullptr;
+            for (auto& e : cache)
+                if (e.n == n && e.ru == ru && e.mask == mask) gph = &e;
+            if (!gph) {
+                BlockGraph e;
+                e.n = n;
+                e.ru = ru;
+                e.mask = mask;
+                e.launches.assign(runs.size(), 0);
+                e.dslash.assign(runs.size(), 0);
+                cudaGraph_t graph;
+                LQ_CUDA(cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal));
+                lqcd_status cs = LQCD_OK;
+                for (size_t i = 0; i < runs.size() && cs == LQCD_OK; ++i) {
+                    if (!(mask >> i & 1)) continue;
+                    lqcd_ctx* c = runs[i]->c;
+                    const long d0 = c->dslash_count, l0 = c->launches;
+                    cs = run_block(runs[i]->s, n, ru);
+                    e.dslash[i] = c->dslash_count - d0;
+                    e.launches[i] = c->launches - l0;
+                    c->dslash_count = d0;
+                    c->launches = l0;
+                }
+                cudaError_t ce = cudaStreamEndCapture(c0->stream, &graph);
+                if (cs != LQCD_OK) { destroy_graphs(cache); return cs; }
+                if (ce != cudaSuccess) { destroy_graphs(cache); return cuda_fail(ce, "cudaStreamEndCapture"); }
+                cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ie != cudaSuccess) { destroy_graphs(cache); return cuda_fail(ie, "cudaGraphInstantiate"); }
+                cache.push_back(e);
+                gph = &cache.back();
+            }
+            cudaError_t le = cudaGraphLaunch(gph->exec, c0->stream);
+            if (le != cudaSuccess) { destroy_graphs(cache); return cuda_fail(le, "cudaGraphLaunch"); }
+            for (size_t i = 0; i < runs.size(); ++i) {
+                runs[i]->c->dslash_count += gph->dslash[i];
+                runs[i]->c->launches += gph->launches[i];
+            }
+        } else {
+            for (size_t i = 0; i < runs.size(); ++i)
+                if (mask >> i & 1) {
+                    lqcd_status bs = run_block(runs[i]->s, n, ru);
+                    if (bs != LQCD_OK) return bs;
+                }
+        }
+        for (size_t i = 0; i < runs.size(); ++i)
+            if (mask >> i & 1) {
+                lqcd_status cs = cg_check(*runs[i], n, ru);
+                if (cs != LQCD_OK && runs[i]->status == LQCD_OK) { destroy_graphs(cache); return cs; }
+            }
+    }
+    destroy_graphs(cache);
+    return LQCD_OK;
+}
+
+}  // namespace
+
+lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, const lqcd_solver_params* p,
+                  lqcd_solver_stats* st)
+{
+    if (p->solver == LQCD_SOLVER_FGCR) {
+        if (R != 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR solves one right-hand side per call");
+        const bool hio = !is_device(b);
+        if (hio != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
+        return solve_fgcr(c, c->precond, x, b, tol, p, st, hio);
+    }
+    CgRun run;
+    LQ_TRY(cg_setup(run, c, x, b, tol, R, p));
+    std::vector<CgRun*> runs{&run};
+    lqcd_status is = iterate(runs, p);
+    if (is != LQCD_OK && run.status == LQCD_OK) return is;
+    return cg_finish(run, st);
+}
+
+// Several lattices solved together: set-up per lattice, then lockstep
+// iteration blocks (one CUDA graph for all lattices with use_graph), then
+// the per-lattice finish.  Every context runs on the stream of ctxs[0]
+// during the call.
+lqcd_status solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b, const double* tol,
+                        const lqcd_solver_params* p, lqcd_solver_stats* st)
+{
+    if (n < 1 || n > 64) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: 1..64 lattices");
+    if (p->solver == LQCD_SOLVER_FGCR) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: CG solvers only");
+    std::vector<cudaStream_t> saved(n);
+    for (int i = 0; i < n; ++i) {
+        saved[i] = ctxs[i]->stream;
+        ctxs[i]->stream = ctxs[0]->stream;
+    }
+    std::vector<CgRun> runs(n);
+    std::vector<CgRun*> ptrs;
+    lqcd_status status = LQCD_OK;
+    for (int i = 0; i < n && status == LQCD_OK; ++i) {
+        status = cg_setup(runs[i], ctxs[i], x[i], b[i], tol[i], 1, p);
+        ptrs.push_back(&runs[i]);
+    }
+    if (status == LQCD_OK) status = iterate(ptrs, p);
+    lqcd_status worst = status;
+    if (status == LQCD_OK || status == LQCD_ERR_BREAKDOWN) {
+        for (int i = 0; i < n; ++i) {
+            lqcd_status fs = cg_finish(runs[i], &st[i]);
+            if (fs != LQCD_OK && worst == LQCD_OK) worst = fs;
+        }
+    }
+    for (int i = 0; i < n; ++i) ctxs[i]->stream = saved[i];
+    return worst;
 }
 
 }  // namespace lqcd

@@ -85,6 +85,8 @@ _SIGS = {
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
+    "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
+                         C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
     "lqcd_net_destroy": [_P],
     "lqcd_net_workspace_size": [_P, C.POINTER(_S)],
@@ -248,6 +250,22 @@ def lqcd_solve(ctx, x, b, tol, nrhs=1, params=None, raise_on_error=True):
 
 def lqcd_sync(ctx):
     _check(_lib.lqcd_sync(ctx), "lqcd_sync")
+
+
+def lqcd_solve_batch(ctxs, xs, bs, tols, params=None, raise_on_error=True):
+    """Solve several lattices together; returns (status, [stats dict])."""
+    n = len(ctxs)
+    if params is None:
+        params = lqcd_solver_params_default()
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    xarr = (C.c_void_p * n)(*[_ptr(x).value for x in xs])
+    barr = (C.c_void_p * n)(*[_ptr(b).value for b in bs])
+    tarr = (C.c_double * n)(*[float(t) for t in tols])
+    st = (lqcd_solver_stats * n)()
+    rc = _lib.lqcd_solve_batch(carr, n, xarr, barr, tarr, C.byref(params), st)
+    if raise_on_error:
+        _check(rc, "lqcd_solve_batch")
+    return rc, [s.as_dict() for s in st]
 
 
 def lqcd_profile_enable(ctx, enable=True):
