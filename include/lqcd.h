@@ -84,7 +84,10 @@ typedef enum {
     LQCD_BF16 = 3,
     LQCD_F16_LINKS = 4,
     LQCD_BF16_LINKS = 5,
-    LQCD_NPREC = 6
+    LQCD_F64_DF = 6,  /* FP64 storage and layout, arithmetic in pairs of FP32
+                         (double-float, ~48-bit significand): FP64-accurate
+                         operator applications at FP32 instruction rate */
+    LQCD_NPREC = 7
 } lqcd_prec;
 
 /* operator selection for lqcd_dslash (op_flags) */
@@ -167,6 +170,10 @@ typedef struct {
     int check_interval;      /* host reads the residual every this many iterations */
     int nkrylov;             /* FGCR restart length */
     int use_graph;           /* 1: replay the iteration block as a CUDA graph */
+    int residual_prec;       /* LQCD_F64 or LQCD_F64_DF: arithmetic of the reliable-update,
+                                candidate-check and FGCR restart residuals of a mixed
+                                solve (an FP64 inner solve always uses LQCD_F64); the
+                                final reported residual is always native FP64 */
 } lqcd_solver_params;
 
 typedef struct {

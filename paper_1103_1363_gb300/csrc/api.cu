@@ -123,7 +123,8 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
     case P16: e = dslash_dispatch_f16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case PB16: e = dslash_dispatch_bf16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case MODE_F16_LINKS: e = dslash_dispatch_f16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
-    default: e = dslash_dispatch_bf16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    case MODE_BF16_LINKS: e = dslash_dispatch_bf16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    default: e = dslash_dispatch_df(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     }
     LQ_CUDA(e);
     if (timed) {
@@ -633,6 +634,7 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
     p->check_interval = 10;
     p->nkrylov = 20;
     p->use_graph = 0;
+    p->residual_prec = LQCD_F64_DF;
     return LQCD_OK;
 }
 

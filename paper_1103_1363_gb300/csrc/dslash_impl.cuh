@@ -179,7 +179,8 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
 #endif
 #define DSLASH_MAX_BLOCK 128
 template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
-__global__ void __launch_bounds__(DSLASH_MAX_BLOCK, (PG == P64 ? 1 : LQCD_DSLASH_MINB)) dslash_kernel(const DslashArgs A)
+__global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 1 : LQCD_DSLASH_MINB))
+    dslash_kernel(const DslashArgs A)
 {
     typedef typename RealT<PS>::type R;
     const int rhs = blockIdx.y;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(DSLASH_MAX_BLOCK, (PG == P64 ? 1 : LQCD_DSLASH
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = t[k] + a * acc[k];
         }
-        if (EPI == EPI_CG) {
+        if constexpr (EPI == EPI_CG) {
             typedef typename RealT<AccumP<PS>::value>::type RA;
             const double* sc = A.scal + rhs * A.scal_rs;
             const RA alpha = (RA)((sc[A.s_num] + sc[A.s_num2]) / (sc[A.s_den] + sc[A.s_den2]));
@@ -285,7 +286,15 @@ cudaError_t dispatch_dslash_p(const DslashArgs& A, int recon, bool dag, int epi,
     LQ_CASE(RC, DG, EPI_XPAY, false)     \
     LQ_CASE(RC, DG, EPI_XPAY, true)      \
     LQ_CASE(RC, DG, EPI_CG, true)
-    if constexpr (PG == P64) {
+    if constexpr (PG == PDF) {
+        // FP64-accurate residuals only: no fused CG update
+        LQ_CASE(18, false, EPI_NONE, false)
+        LQ_CASE(18, false, EPI_CLOVINV, false)
+        LQ_CASE(18, false, EPI_XPAY, false)
+        LQ_CASE(18, true, EPI_NONE, false)
+        LQ_CASE(18, true, EPI_CLOVINV, false)
+        LQ_CASE(18, true, EPI_XPAY, false)
+    } else if constexpr (PG == P64) {
         LQ_EPIS(18, false)
         LQ_EPIS(18, true)
     } else {

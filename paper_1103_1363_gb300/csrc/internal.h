@@ -53,6 +53,7 @@ cudaError_t dslash_dispatch_f16(const DslashArgs&, int, bool, int, bool, int, in
 cudaError_t dslash_dispatch_bf16(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_f16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_bf16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
+cudaError_t dslash_dispatch_df(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 
 struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 

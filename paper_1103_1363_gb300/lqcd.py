@@ -28,12 +28,12 @@ _lib = C.CDLL(LIB_PATH)
 LQCD_OK = 0
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_STATE",
           5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_CLOVER_SINGULAR"}
-F64, F32, F16, BF16, F16_LINKS, BF16_LINKS = 0, 1, 2, 3, 4, 5
+F64, F32, F16, BF16, F16_LINKS, BF16_LINKS, F64_DF = 0, 1, 2, 3, 4, 5, 6
 PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "f16links": F16_LINKS,
-        "bf16links": BF16_LINKS}
-PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links")
+        "bf16links": BF16_LINKS, "f64df": F64_DF}
+PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df")
 # storage precision of links / clover for each mode (the bit it needs in prec_mask)
-_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16}
+_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16, F64_DF: F64}
 OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
 SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR = 0, 1, 2
 
@@ -46,7 +46,8 @@ class lqcd_config(C.Structure):
 class lqcd_solver_params(C.Structure):
     _fields_ = [("solver", C.c_int), ("inner_prec", C.c_int), ("maxiter", C.c_int),
                 ("reliable_interval", C.c_int), ("reliable_delta", C.c_double),
-                ("check_interval", C.c_int), ("nkrylov", C.c_int), ("use_graph", C.c_int)]
+                ("check_interval", C.c_int), ("nkrylov", C.c_int), ("use_graph", C.c_int),
+                ("residual_prec", C.c_int)]
 
 
 class lqcd_solver_stats(C.Structure):
@@ -283,7 +284,7 @@ def lqcd_profile_read(ctx):
 def solver_params(**kw):
     p = lqcd_solver_params_default()
     for k, v in kw.items():
-        if k == "inner_prec":
+        if k in ("inner_prec", "residual_prec"):
             v = PREC.get(v, v)
         setattr(p, k, v)
     return p
