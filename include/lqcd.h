@@ -170,10 +170,11 @@ typedef struct {
     int check_interval;      /* host reads the residual every this many iterations */
     int nkrylov;             /* FGCR restart length */
     int use_graph;           /* 1: replay the iteration block as a CUDA graph */
-    int residual_prec;       /* LQCD_F64 or LQCD_F64_DF: arithmetic of the reliable-update,
-                                candidate-check and FGCR restart residuals of a mixed
-                                solve (an FP64 inner solve always uses LQCD_F64); the
-                                final reported residual is always native FP64 */
+    int residual_prec;       /* LQCD_F64 (default) or LQCD_F64_DF: arithmetic of the
+                                reliable-update, candidate-check and FGCR restart
+                                residuals of a mixed solve (an FP64 inner solve always
+                                uses LQCD_F64); the final reported residual is always
+                                native FP64 */
 } lqcd_solver_params;
 
 typedef struct {

@@ -634,7 +634,9 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
     p->check_interval = 10;
     p->nkrylov = 20;
     p->use_graph = 0;
-    p->residual_prec = LQCD_F64_DF;
+    // native FP64: the double-float kernels measured slower on GB300 (255
+    // registers, one 4-warp block per SM, dependent FP32 chains)
+    p->residual_prec = LQCD_F64;
     return LQCD_OK;
 }
 
