@@ -274,6 +274,46 @@ def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
             "time_roofline_frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": hbsrc}
 
 
+def run_hop_kernel(args, w):
+    """Stand-alone parity hopping term (recon-12) of one precision, for kernel
+    profiles: warmup + steps launches over 8 rotating buffer pairs."""
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import lqcd
+    dims = w["dims"]
+    Vh = int(np.prod(dims)) // 2
+    stream = torch.cuda.Stream()
+    lat = lqcd.Lattice(dims, precisions=("f64", args.prec), recon=12, stream=stream)
+    lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
+    b = synth.gaussian_spinor(dims, w["src_seed"])
+    nbuf = 8
+    with torch.cuda.stream(stream):
+        fins = [lat.new_field(args.prec) for _ in range(nbuf)]
+        fouts = [lat.new_field(args.prec) for _ in range(nbuf)]
+    for f in fins:
+        lat.pack(f, b, 1, args.prec)
+    for i in range(args.warmup):
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec)
+    e1.record(stream)
+    stream.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / args.steps
+    sb = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52}[args.prec]
+    lb = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24}[args.prec]
+    comp = (2 * sb + 8 * lb) * Vh
+    hb, src = measured_peaks()
+    print(json.dumps({"kernel": "hop", "prec": args.prec, "workload": workload_name(w),
+                      "us_per_launch": round(t * 1e6, 2), "gflops": round(1320.0 * Vh / t / 1e9, 1),
+                      "compulsory_bytes": comp, "achieved_gbs": round(comp / t / 1e9, 1),
+                      "frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": src}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------ oracle (CPU)
 
 def oracle_sample(w, napply):
@@ -332,11 +372,16 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the comparison legs")
     ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links"],
                     help="storage of the timed solve's inner iteration")
+    ap.add_argument("--kernel", default=None, choices=["hop"],
+                    help="instead of the solve: time the stand-alone parity hopping kernel (profiling)")
+    ap.add_argument("--prec", default="f16", help="precision of --kernel hop")
     ap.add_argument("--cpu-applications", type=int, default=3)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.kernel == "hop":
+        return run_hop_kernel(args, w)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
