@@ -284,7 +284,7 @@ def run_hop_kernel(args, w):
     dims = w["dims"]
     Vh = int(np.prod(dims)) // 2
     stream = torch.cuda.Stream()
-    lat = lqcd.Lattice(dims, precisions=("f64", args.prec), recon=12, stream=stream)
+    lat = lqcd.Lattice(dims, precisions=("f64", args.prec), recon=args.recon, stream=stream)
     lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
     b = synth.gaussian_spinor(dims, w["src_seed"])
     nbuf = 8
@@ -304,10 +304,10 @@ def run_hop_kernel(args, w):
     stream.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / args.steps
     sb = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52}[args.prec]
-    lb = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24}[args.prec]
+    lb = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24}[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
     comp = (2 * sb + 8 * lb) * Vh
     hb, src = measured_peaks()
-    print(json.dumps({"kernel": "hop", "prec": args.prec, "workload": workload_name(w),
+    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "workload": workload_name(w),
                       "us_per_launch": round(t * 1e6, 2), "gflops": round(1320.0 * Vh / t / 1e9, 1),
                       "compulsory_bytes": comp, "achieved_gbs": round(comp / t / 1e9, 1),
                       "frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": src}), flush=True)
@@ -375,6 +375,7 @@ def main():
     ap.add_argument("--kernel", default=None, choices=["hop"],
                     help="instead of the solve: time the stand-alone parity hopping kernel (profiling)")
     ap.add_argument("--prec", default="f16", help="precision of --kernel hop")
+    ap.add_argument("--recon", type=int, default=12, choices=[12, 18], help="link storage of --kernel hop")
     ap.add_argument("--cpu-applications", type=int, default=3)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]

@@ -176,10 +176,11 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
 // before hop d is decoded and computed, so that two hops' loads are in
 // flight per thread: half-precision loads move few bytes each, and one hop
 // at a time does not cover DRAM latency.
+template <int RECON>
 struct HalfHopRaw {
     uint4 s[3];
     float n;
-    uint2 u[3];
+    uint32_t u[RECON == 12 ? 6 : 9];  // packed half2: two (recon-12) or three rows
 };
 
 struct HopPlan {
@@ -188,8 +189,9 @@ struct HopPlan {
     unsigned flip;  // bit h: the hop crosses the antiperiodic t boundary
 };
 
+template <int RECON>
 __device__ __forceinline__ void load_half_hop(const char* in, const void* gauge, int stride, int par,
-                                              const HopPlan& hp, int h, HalfHopRaw& r)
+                                              const HopPlan& hp, int h, HalfHopRaw<RECON>& r)
 {
     const uint4* sp = reinterpret_cast<const uint4*>(in);
     const int j = hp.nb[h];
@@ -197,52 +199,62 @@ __device__ __forceinline__ void load_half_hop(const char* in, const void* gauge,
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.s[k] = __ldg(sp + (size_t)k * stride + j);
     const int mu = h >> 1, lpar = (h & 1) ? 1 - par : par;
-    const uint2* lp = static_cast<const uint2*>(gauge) + (size_t)((lpar * 4 + mu) * 3) * stride + hp.lidx[h];
+    if constexpr (RECON == 12) {
+        const uint2* lp = static_cast<const uint2*>(gauge) + (size_t)((lpar * 4 + mu) * 3) * stride + hp.lidx[h];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r.u[k] = __ldg(lp + (size_t)k * stride);
+        for (int k = 0; k < 3; ++k) {
+            const uint2 q = __ldg(lp + (size_t)k * stride);
+            r.u[2 * k] = q.x;
+            r.u[2 * k + 1] = q.y;
+        }
+    } else {
+        const uint32_t* lp = static_cast<const uint32_t*>(gauge) + (size_t)((lpar * 4 + mu) * 9) * stride + hp.lidx[h];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) r.u[k] = __ldg(lp + (size_t)k * stride);
+    }
 }
 
-template <int ISBF, int MU, bool BWD, bool DAG>
-__device__ __forceinline__ void compute_half_hop(const HalfHopRaw& r, bool flip, float acc[24])
+template <int ISBF, int RECON, int MU, bool BWD, bool DAG>
+__device__ __forceinline__ void compute_half_hop(const HalfHopRaw<RECON>& r, bool flip, float acc[24])
 {
     float v[24], h[12], u[18], w[12];
+    // decode without the norm: the projection is linear, so the norm (and the
+    // boundary sign) scale the 12 projected values instead of the 24 inputs
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const uint4 c = r.s[k];
         const float2 a = h2f(c.x, ISBF), b = h2f(c.y, ISBF), d = h2f(c.z, ISBF), e = h2f(c.w, ISBF);
-        v[8 * k + 0] = a.x * r.n; v[8 * k + 1] = a.y * r.n;
-        v[8 * k + 2] = b.x * r.n; v[8 * k + 3] = b.y * r.n;
-        v[8 * k + 4] = d.x * r.n; v[8 * k + 5] = d.y * r.n;
-        v[8 * k + 6] = e.x * r.n; v[8 * k + 7] = e.y * r.n;
+        v[8 * k + 0] = a.x; v[8 * k + 1] = a.y; v[8 * k + 2] = b.x; v[8 * k + 3] = b.y;
+        v[8 * k + 4] = d.x; v[8 * k + 5] = d.y; v[8 * k + 6] = e.x; v[8 * k + 7] = e.y;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float2 a = h2f(r.u[k].x, ISBF), b = h2f(r.u[k].y, ISBF);
-        u[4 * k] = a.x; u[4 * k + 1] = a.y; u[4 * k + 2] = b.x; u[4 * k + 3] = b.y;
+    for (int k = 0; k < (RECON == 12 ? 6 : 9); ++k) {
+        const float2 a = h2f(r.u[k], ISBF);
+        u[2 * k] = a.x;
+        u[2 * k + 1] = a.y;
     }
-    reconstruct_row2(u);
+    if constexpr (RECON == 12) reconstruct_row2(u);
     constexpr int S = (BWD != DAG) ? +1 : -1;  // forward (1 - g), backward (1 + g); swapped by DAG
     project<MU, S>(v, h);
-    if (flip) {
+    const float scale = flip ? -r.n : r.n;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) h[k] = -h[k];
-    }
+    for (int k = 0; k < 12; ++k) h[k] *= scale;
     su3_mul_half<BWD>(u, h, w);
     accumulate<MU, S>(acc, w);
 }
 
-template <int ISBF, bool DAG, int H>
+template <int ISBF, int RECON, bool DAG, int H>
 __device__ __forceinline__ void half_pipeline_step(const char* in, const void* gauge, int stride, int par,
-                                                   const HopPlan& hp, HalfHopRaw (&buf)[2], float acc[24])
+                                                   const HopPlan& hp, HalfHopRaw<RECON> (&buf)[2], float acc[24])
 {
-    if constexpr (H < 7) load_half_hop(in, gauge, stride, par, hp, H + 1, buf[(H + 1) & 1]);
-    compute_half_hop<ISBF, H / 2, (H & 1) != 0, DAG>(buf[H & 1], (hp.flip >> H) & 1u, acc);
-    if constexpr (H < 7) half_pipeline_step<ISBF, DAG, H + 1>(in, gauge, stride, par, hp, buf, acc);
+    if constexpr (H < 7) load_half_hop<RECON>(in, gauge, stride, par, hp, H + 1, buf[(H + 1) & 1]);
+    compute_half_hop<ISBF, RECON, H / 2, (H & 1) != 0, DAG>(buf[H & 1], (hp.flip >> H) & 1u, acc);
+    if constexpr (H < 7) half_pipeline_step<ISBF, RECON, DAG, H + 1>(in, gauge, stride, par, hp, buf, acc);
 }
 
-template <int ISBF, bool DAG>
-__device__ __forceinline__ void hop_all_half_r12(const DslashArgs& A, const char* in, int i, int full, const int c[4],
-                                                 float acc[24])
+template <int ISBF, int RECON, bool DAG>
+__device__ __forceinline__ void hop_all_half(const DslashArgs& A, const char* in, int i, int full, const int c[4],
+                                             float acc[24])
 {
     HopPlan hp;
     hp.flip = 0u;
@@ -262,9 +274,9 @@ __device__ __forceinline__ void hop_all_half_r12(const DslashArgs& A, const char
         if (c[3] == A.g.L[3] - 1) hp.flip |= 1u << 6;
         if (c[3] == 0) hp.flip |= 1u << 7;
     }
-    HalfHopRaw buf[2];
-    load_half_hop(in, A.gauge, A.g.stride, A.par, hp, 0, buf[0]);
-    half_pipeline_step<ISBF, DAG, 0>(in, A.gauge, A.g.stride, A.par, hp, buf, acc);
+    HalfHopRaw<RECON> buf[2];
+    load_half_hop<RECON>(in, A.gauge, A.g.stride, A.par, hp, 0, buf[0]);
+    half_pipeline_step<ISBF, RECON, DAG, 0>(in, A.gauge, A.g.stride, A.par, hp, buf, acc);
 }
 
 // Threads per block are at most DSLASH_MAX_BLOCK; DSLASH_MIN_BLOCKS resident
@@ -292,8 +304,8 @@ __global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 
         R acc[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = 0;
-        if constexpr ((PS == P16 || PS == PB16) && PG == PS && RECON == 12) {
-            hop_all_half_r12<PS == PB16 ? 1 : 0, DAG>(A, in, i, full, c, acc);
+        if constexpr ((PS == P16 || PS == PB16) && PG == PS) {
+            hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG>(A, in, i, full, c, acc);
         } else {
             hop_dir<PG, PS, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
             hop_dir<PG, PS, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
