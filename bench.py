@@ -108,6 +108,28 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------- replica aggregation
+# Each rank solves its own copy of the workload (the solve does not shard
+# across GPUs here); the job's time is the slowest rank's, its work the sum.
+
+def reduce_max(value, device):
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, device):
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, w, rank, world, local_rank):
@@ -136,6 +158,7 @@ def run_ours(args, w, rank, world, local_rank):
     t0 = time.time()
     lat.clover_compute(w["kappa"], w["csw"])
     clover_s = time.time() - t0
+    tuned = {p: lqcd.lqcd_tune(lat.ctx, p) for p in ("f64", args.inner)}  # block sizes (plain, dagger)
     del Ud
     params = dict(inner_prec=args.inner, reliable_interval=50, check_interval=10)
 
@@ -165,12 +188,9 @@ def run_ours(args, w, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     prof = lqcd.lqcd_profile_read(lat.ctx)
     lqcd.lqcd_profile_enable(lat.ctx, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dev)
     dslash_total = sum(s["dslash_count"] for s in stats)
-    flops = dslash_total * 1320.0 * Vh * world
+    flops = reduce_sum(dslash_total * 1320.0 * Vh, dev)
     value = flops / (ms * 1e-3) / 1e9
     worst_res = max(s["true_residual"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
@@ -189,7 +209,7 @@ def run_ours(args, w, rank, world, local_rank):
 
     out = {"value": value, "ms": ms, "stats": stats, "roofline": roofline, "clocks": clk,
            "dslash_total": dslash_total, "worst_res": worst_res, "launches": launches,
-           "clover_setup_s": round(clover_s, 3), "prof": prof}
+           "clover_setup_s": round(clover_s, 3), "prof": prof, "tuned_block": tuned}
 
     if rank == 0 and not args.quick:
         out["e2e"] = e2e_leg(args, lat, b, Vh, params)
@@ -415,7 +435,7 @@ def main():
                                "reliable_updates": r["stats"][-1]["reliable_updates"],
                                "dslash": r["stats"][-1]["dslash_count"],
                                "true_residual_max": r["worst_res"]},
-            "clover_setup_s": r["clover_setup_s"],
+            "clover_setup_s": r["clover_setup_s"], "tuned_block": r["tuned_block"],
             "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"),
         }
         print(json.dumps(line), flush=True)

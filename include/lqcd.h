@@ -282,6 +282,14 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 
+/* Autotuner: time the hopping kernels of precision `prec` (plain and dagger,
+ * x-pay epilogue as in the solvers) at 32, 64, 96 and 128 threads per block
+ * on this context's lattice and keep the fastest for every later launch.
+ * Needs a loaded gauge field; overwrites the solver vectors of the
+ * workspace.  best_block (may be NULL) receives the choice for plain [0]
+ * and dagger [1].  Synchronises the stream. */
+lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[2]);
+
 /* Kernel timing.  While enabled, every hopping-term launch the context
  * issues is bracketed by CUDA events on its stream (graph replays are not
  * recorded).  lqcd_profile_read waits for the stream and returns, for each

@@ -616,6 +616,53 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
     LQ_GUARD_END
 }
 
+lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[2])
+{
+    LQ_GUARD_BEGIN
+    LQ_TRY(check_ready(c));
+    LQ_TRY(check_prec(c, prec));
+    if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_tune: no gauge field loaded");
+    LQ_TRY(set_device_of(c));
+    // scratch: two full fields of the FP64-sized solver vectors, zeroed
+    const size_t fb = c->field_bytes(prec);
+    char* in = vec64_field(c, 0, 0);
+    char* out = vec64_field(c, 1, 0);
+    LQ_CUDA(cudaMemsetAsync(in, 0, 2 * fb, c->stream));
+    cudaEvent_t e0, e1;
+    LQ_CUDA(cudaEventCreate(&e0));
+    LQ_CUDA(cudaEventCreate(&e1));
+    const int cands[4] = {32, 64, 96, 128};
+    lqcd_status st = LQCD_OK;
+    for (int dag = 0; dag < 2 && st == LQCD_OK; ++dag) {
+        float best = 1e30f;
+        int best_b = DSLASH_MAX_BLOCK;
+        for (int ci = 0; ci < 4 && st == LQCD_OK; ++ci) {
+            c->tuned_block[prec][dag] = cands[ci];
+            float ms = 0.f;
+            for (int rep = 0; rep < 4 && st == LQCD_OK; ++rep) {  // rep 0 warms up
+                if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+                if (st == LQCD_OK)
+                    st = op_hop(c, out + fb, in, 1, prec, dag != 0, EPI_XPAY, false, nullptr, in + fb, -0.1, 1, fb, -1);
+                if (st == LQCD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess)
+                    st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+                if (st == LQCD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: sync");
+                float t = 0.f;
+                if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+            }
+            if (st == LQCD_OK && ms < best) {
+                best = ms;
+                best_b = cands[ci];
+            }
+        }
+        c->tuned_block[prec][dag] = best_b;
+        if (best_block) best_block[dag] = best_b;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+    LQ_GUARD_END
+}
+
 lqcd_status lqcd_set_preconditioner(lqcd_ctx* c, lqcd_net* net)
 {
     if (!c) return fail(LQCD_ERR_INVALID, "null context");

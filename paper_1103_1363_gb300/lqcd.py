@@ -86,6 +86,7 @@ _SIGS = {
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
+    "lqcd_tune": [_P, _I, C.POINTER(C.c_int)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
@@ -267,6 +268,13 @@ def lqcd_solve_batch(ctxs, xs, bs, tols, params=None, raise_on_error=True):
     if raise_on_error:
         _check(rc, "lqcd_solve_batch")
     return rc, [s.as_dict() for s in st]
+
+
+def lqcd_tune(ctx, prec):
+    """Autotune the hopping kernels' block size; returns (plain, dagger) choices."""
+    best = (C.c_int * 2)()
+    _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best), "lqcd_tune")
+    return best[0], best[1]
 
 
 def lqcd_profile_enable(ctx, enable=True):
