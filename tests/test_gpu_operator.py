@@ -189,3 +189,18 @@ def test_hop_full_size_sampled(lq):
         err = rel(g, want)
         print("full-size hop par %d: %.3e" % (par, err))
         assert err < 1e-6
+
+
+def test_autotuner_keeps_results(lq):
+    """lqcd_tune picks a block size per precision and dagger; results are
+    unchanged by the choice."""
+    dims = (8, 8, 8, 8)
+    U = gauge(dims, "haar", seed=17)
+    psi = synth.gaussian_spinor(dims, 18)
+    lat = lq.Lattice(dims)
+    lat.gauge_load(U)
+    for prec in ("f32", "f16"):
+        best = lq.lqcd_tune(lat.ctx, prec)
+        assert all(b in (32, 64, 96, 128) for b in best)
+        got = gpu_apply(lat, prec, psi, 1, 0, lambda o, i: lat.dslash(o, i, 0, prec=prec))
+        assert rel(got, hop_ref(U, psi, dims, 0)) < TOL[prec]
