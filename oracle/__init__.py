@@ -64,6 +64,7 @@ _SIGS = {
     "oracle_net_layer_adj": (None, [_P, _I, _P, _I, _I, _P, _P, _P]),
     "oracle_net_layer_wgrad": (None, [_P, _I, _P, _I, _I, _P, _P, _P]),
     "oracle_fgcr": (_I, [_P, _I, _P, _P, _D, _P, _P, _D, _I, _I, _PREC, _P, _P, _P]),
+    "oracle_sap": (None, [_P, _I, _P, _P, _D, _P, _I, _I, _P, _P]),
 }
 
 
@@ -286,6 +287,17 @@ def net_layer_wgrad(U, psi, g, cout, tanti=1):
     lib().oracle_net_layer_wgrad(_dims(dims_of(U)), tanti, _p(U), cin, cout, _p(psi), _p(g),
                                  _p(gW))
     return gW
+
+
+def sap(U, A, kappa, r, block, ncycle=1, nmr=4, tanti=1):
+    """Schwarz alternating procedure (block MR with Dirichlet boundaries,
+    checkerboard-coloured blocks): z ~ M^{-1} r."""
+    U, r = _c(U), _c(r)
+    A = None if A is None else _c(A)
+    z = np.empty_like(r)
+    bs = (C.c_int * 4)(*[int(v) for v in block])
+    lib().oracle_sap(_dims(dims_of(U)), tanti, _p(U), _Aptr(A), kappa, bs, ncycle, nmr, _p(r), _p(z))
+    return z
 
 
 def fgcr(U, A, kappa, b, tol=1e-10, nkrylov=20, maxiter=100000, prec=None, tanti=1):

@@ -763,6 +763,84 @@ void oracle_net_layer_wgrad(const int d[4], int tanti, const cplx *U, int cin, i
     free(tr);
 }
 
+/* ----------------------------------------------------------------- SAP */
+
+/*
+ * Schwarz alternating procedure as a preconditioner (Sec. 5): the lattice is
+ * divided into non-overlapping blocks of extent bs[mu] (every lattice extent
+ * a multiple of bs[mu] with an even number >= 2 of blocks per direction), and
+ * the blocks are coloured like a checkerboard by the parity of the sum of
+ * their block coordinates.  Starting from z = 0, each of ncycle cycles
+ * solves on all colour-0 blocks, updates the residual, solves on all
+ * colour-1 blocks and updates the residual.  A block solve is nmr iterations
+ * of minimal residual (MR) on the block operator with Dirichlet boundary
+ * conditions, M_B = P_B M P_B (P_B restricts to the block), starting from 0:
+ *   q = M_B rho;  alpha = <q, rho> / <q, q>;  delta += alpha rho;  rho -= alpha q.
+ * Output z approximates M^{-1} r.
+ */
+static int block_colour(const int d[4], const int bs[4], const int c[4])
+{
+    (void)d;
+    return (c[0] / bs[0] + c[1] / bs[1] + c[2] / bs[2] + c[3] / bs[3]) & 1;
+}
+
+static long block_id(const int d[4], const int bs[4], const int c[4])
+{
+    const int nb0 = d[0] / bs[0], nb1 = d[1] / bs[1], nb2 = d[2] / bs[2];
+    return ((long)(c[3] / bs[3] * nb2 + c[2] / bs[2]) * nb1 + c[1] / bs[1]) * nb0 + c[0] / bs[0];
+}
+
+void oracle_sap(const int d[4], int tanti, const cplx *U, const cplx *A, double kappa, const int bs[4],
+                int ncycle, int nmr, const cplx *r, cplx *z)
+{
+    long V = volume(d), n = 12 * V;
+    long nblocks = V / ((long)bs[0] * bs[1] * bs[2] * bs[3]);
+    long *bid = malloc(sizeof(long) * V);
+    int *col = malloc(sizeof(int) * V);
+    for (long x = 0; x < V; ++x) {
+        int c[4];
+        coords(d, x, c);
+        bid[x] = block_id(d, bs, c);
+        col[x] = block_colour(d, bs, c);
+    }
+    cplx *rho = malloc(sizeof(cplx) * n), *q = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+    cplx *blk = malloc(sizeof(cplx) * n);
+    memset(z, 0, sizeof(cplx) * n);
+    for (int cy = 0; cy < ncycle; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            /* residual of the current z */
+            oracle_wilson_clover(d, tanti, U, A, kappa, z, t);
+            for (long i = 0; i < n; ++i) rho[i] = r[i] - t[i];
+            for (long b = 0; b < nblocks; ++b) {
+                /* is this block of the colour being solved? */
+                int is_col = -1;
+                for (long x = 0; x < V && is_col < 0; ++x)
+                    if (bid[x] == b) is_col = col[x] == colour;
+                if (!is_col) continue;
+                /* rho_B and delta on the block */
+                memset(blk, 0, sizeof(cplx) * n);
+                for (long x = 0; x < V; ++x)
+                    if (bid[x] == b) memcpy(blk + 12 * x, rho + 12 * x, 12 * sizeof(cplx));
+                cplx *delta = t;
+                memset(delta, 0, sizeof(cplx) * n);
+                for (int it = 0; it < nmr; ++it) {
+                    oracle_wilson_clover(d, tanti, U, A, kappa, blk, q); /* blk is zero off the block */
+                    for (long x = 0; x < V; ++x)
+                        if (bid[x] != b) memset(q + 12 * x, 0, 12 * sizeof(cplx));
+                    cplx qr = cdot(n, q, blk);
+                    double qq = norm2(n, q);
+                    if (qq == 0.0) break;
+                    cplx alpha = qr / qq;
+                    for (long i = 0; i < n; ++i) { delta[i] += alpha * blk[i]; blk[i] -= alpha * q[i]; }
+                }
+                for (long x = 0; x < V; ++x)
+                    if (bid[x] == b)
+                        for (int k = 0; k < 12; ++k) z[12 * x + k] += delta[12 * x + k];
+            }
+        }
+    free(bid); free(col); free(rho); free(q); free(t); free(blk);
+}
+
 /* ---------------------------------------------------------------- FGCR */
 
 /*

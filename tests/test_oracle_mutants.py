@@ -12,6 +12,7 @@ import pytest
 import oracle
 from tests import test_oracle_pins as P
 from tests import test_oracle_net_pins as NP
+from tests import test_oracle_sap_pins as SP
 
 MUTANTS = {
     "forward_projector_1_g": ("add_hop(out, g, -1.0, link(U, x, mu)",
@@ -35,6 +36,9 @@ MUTANTS = {
                                       "if (fwd) mat3_dag(link(U, x, mu), V);"),
     "wgrad_missing_conj": ("acc += g[3 * i + a] * conj(tr[3 * j + a]);",
                            "acc += g[3 * i + a] * tr[3 * j + a];"),
+    "sap_no_dirichlet": ("if (bid[x] != b) memset(q + 12 * x, 0, 12 * sizeof(cplx));", ""),
+    "sap_block_colour": ("return (c[0] / bs[0] + c[1] / bs[1] + c[2] / bs[2] + c[3] / bs[3]) & 1;",
+                         "return (c[0] / bs[0] + c[1] / bs[1] + c[2] / bs[2]) & 1;"),
 }
 
 PINS = [
@@ -46,6 +50,8 @@ PINS = [
     lambda: P.test_clover_constant_abelian_field(0, 1, 1),
     NP.test_layer_reduces_to_wilson_operator,
     NP.test_weight_gradient_finite_differences,
+    SP.test_exact_block_solves_clear_last_colour,
+    SP.test_block_solve_matches_dense_dirichlet_solve,
     P.test_solvers_against_dense_solve,  # slowest last
 ]
 
