@@ -36,7 +36,7 @@ MUTANTS = {
                                       "if (fwd) mat3_dag(link(U, x, mu), V);"),
     "wgrad_missing_conj": ("acc += g[3 * i + a] * conj(tr[3 * j + a]);",
                            "acc += g[3 * i + a] * tr[3 * j + a];"),
-    "sap_no_dirichlet": ("if (bid[x] != b) memset(q + 12 * x, 0, 12 * sizeof(cplx));", ""),
+    "sap_no_dirichlet": ("if (bid[x] != b) memset(q + 12 * x, 0, 12 * sizeof(cplx));", ";"),
     "sap_block_colour": ("return (c[0] / bs[0] + c[1] / bs[1] + c[2] / bs[2] + c[3] / bs[3]) & 1;",
                          "return (c[0] / bs[0] + c[1] / bs[1] + c[2] / bs[2]) & 1;"),
 }
