@@ -334,6 +334,81 @@ def run_hop_kernel(args, w):
     return 0
 
 
+def sap_block_flops(block):
+    """FP32 flops per site and MR iteration of the SAP block solve: the
+    block-restricted hops (165 each: projection, two SU(3) x vector products,
+    reconstruction), the clover term (504), and the MR vector work (384:
+    q = A rho - kappa h, |q|^2, <q, rho>, z += a rho, rho -= a q)."""
+    hops = sum(2.0 * (b - 1) / b for b in block)
+    return 165.0 * hops + 504.0 + 384.0
+
+
+def run_sap_kernel(args, w):
+    """SAP on the workload's lattice: the application z = SAP(r) alone
+    (rotating buffers, larger than L2), then SAP-FGCR against identity-FGCR
+    and the FP16-inner even-odd CG to the same tolerance."""
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import lqcd
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    block = tuple(int(b) for b in args.block.split("x"))
+    K = 16
+    stream = torch.cuda.Stream()
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16"), recon=12, gcr_nkrylov=K, stream=stream)
+    lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
+    lat.clover_compute(w["kappa"], w["csw"])
+    b = synth.gaussian_spinor(dims, w["src_seed"])
+    nbuf = 4
+    with torch.cuda.stream(stream):
+        rs = [lat.new_field("f32", full=True) for _ in range(nbuf)]
+        zs = [lat.new_field("f32", full=True) for _ in range(nbuf)]
+    for f in rs:
+        lat.pack(f, b, -1, "f32")
+    for i in range(args.warmup):
+        lat.sap_apply(zs[i % nbuf], rs[i % nbuf], block, args.ncycle, args.nmr)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        lat.sap_apply(zs[i % nbuf], rs[i % nbuf], block, args.ncycle, args.nmr)
+    e1.record(stream)
+    stream.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / args.steps
+    fl = sap_block_flops(block) * args.nmr * args.ncycle * V
+    out = {"kernel": "sap", "workload": workload_name(w), "block": list(block), "ncycle": args.ncycle,
+           "nmr": args.nmr, "ms_per_application": round(t * 1e3, 3),
+           "block_solve_flops_per_application": fl, "block_solve_gflops": round(fl / t / 1e9, 1)}
+    del rs, zs
+    if args.quick:
+        print(json.dumps(out), flush=True)
+        return 0
+    bd = torch.from_numpy(b).cuda()
+    xd = lat.canonical_spinor()
+    solves = {}
+    for name, sap, kw in (("fgcr_sap", True, dict(solver=lqcd.SOLVER_FGCR, inner_prec="f32", nkrylov=K)),
+                          ("eo_cg_f16_inner", False, dict(inner_prec="f16", reliable_interval=50,
+                                                          check_interval=10)),
+                          ("fgcr_identity", False, dict(solver=lqcd.SOLVER_FGCR, inner_prec="f32", nkrylov=K,
+                                                        maxiter=20000))):
+        lat.set_sap(block if sap else None, args.ncycle, args.nmr)
+        if name != "fgcr_identity":
+            lat.solve(xd, bd, TOL, raise_on_error=False, **kw)  # warm-up (graphs, first-touch)
+        stream.synchronize()
+        e0.record(stream)
+        rc, st = lat.solve(xd, bd, TOL, raise_on_error=False, **kw)
+        e1.record(stream)
+        stream.synchronize()
+        solves[name] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "iterations": st["iterations"],
+                        "true_residual": st["true_residual"], "status": rc,
+                        "fallback": st["preconditioner_fallback"]}
+    lat.set_sap(None)
+    out["solves"] = solves
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------ oracle (CPU)
 
 def oracle_sample(w, napply):
@@ -389,11 +464,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32c64", choices=sorted(WORKLOADS))
-    ap.add_argument("--quick", action="store_true", help="skip the comparison legs")
+    ap.add_argument("--quick", action="store_true", help="skip the comparison legs (and the solves of --kernel sap)")
     ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links"],
                     help="storage of the timed solve's inner iteration")
-    ap.add_argument("--kernel", default=None, choices=["hop"],
-                    help="instead of the solve: time the stand-alone parity hopping kernel (profiling)")
+    ap.add_argument("--kernel", default=None, choices=["hop", "sap"],
+                    help="instead of the solve: time the stand-alone parity hopping kernel, or the SAP "
+                         "preconditioner and SAP-FGCR (profiling)")
+    ap.add_argument("--block", default="4x4x4x4", help="SAP block extents of --kernel sap")
+    ap.add_argument("--ncycle", type=int, default=5, help="SAP cycles of --kernel sap")
+    ap.add_argument("--nmr", type=int, default=4, help="MR iterations per block of --kernel sap")
     ap.add_argument("--prec", default="f16", help="precision of --kernel hop")
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18], help="link storage of --kernel hop")
     ap.add_argument("--cpu-applications", type=int, default=3)
@@ -403,6 +482,8 @@ def main():
         return run_reference(args, w)
     if args.kernel == "hop":
         return run_hop_kernel(args, w)
+    if args.kernel == "sap":
+        return run_sap_kernel(args, w)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

@@ -269,6 +269,31 @@ lqcd_status lqcd_net_train_step(lqcd_net* net, const float* r, const float* e, i
  * GCR).  The network must belong to this context and outlive its use. */
 lqcd_status lqcd_set_preconditioner(lqcd_ctx* ctx, lqcd_net* net);
 
+/* Schwarz alternating procedure (Sec. 5, the SAP preconditioner of the
+ * SAP-FGCR solver): the lattice is cut into non-overlapping blocks of
+ * block[0] x block[1] x block[2] x block[3] sites, coloured by the parity of
+ * the sum of the block coordinates.  Starting from z = 0, each of `ncycle`
+ * cycles takes the blocks of colour 0 and then those of colour 1; for one
+ * colour the residual rho = r - M z is formed, every block of that colour
+ * runs `nmr` minimal-residual iterations on M_B delta = rho_B (M restricted
+ * to the block: hops leaving it are dropped, i.e. Dirichlet boundaries) and
+ * z += delta on the block.  M = A - kappa H with the kappa and clover of the
+ * last lqcd_clover_compute (A = 1 when csw = 0).
+ *
+ * lqcd_set_preconditioner_sap makes SAP the right preconditioner of
+ * LQCD_SOLVER_FGCR (it replaces a network set by lqcd_set_preconditioner,
+ * and setting a network replaces SAP); block = NULL switches it off.
+ * lqcd_sap_apply computes z = SAP(r) once.  z and r: device pointers to
+ * FP32 full fields in the internal layout (lqcd_field_bytes(ctx, LQCD_F32)
+ * bytes per parity, even then odd; pack with parity -1), z != r.  Uses the
+ * solver vectors of the workspace as scratch; asynchronous on the stream.
+ * Requirements (LQCD_ERR_INVALID otherwise): every block extent divides the
+ * lattice extent with an even number (>= 2) of blocks per direction, at most
+ * 1024 sites per block, ncycle >= 1, nmr >= 1; the context must hold FP32
+ * links (LQCD_ERR_STATE). */
+lqcd_status lqcd_set_preconditioner_sap(lqcd_ctx* ctx, const int block[4], int ncycle, int nmr);
+lqcd_status lqcd_sap_apply(lqcd_ctx* ctx, void* z, const void* r, const int block[4], int ncycle, int nmr);
+
 /* Solve the systems of n contexts (lattices of any sizes, one right-hand
  * side each, canonical FP64 x[i], b[i] on host or device) together with a
  * CG solver: set-up per lattice, then iteration blocks in lockstep on the

@@ -667,6 +667,7 @@ lqcd_status lqcd_set_preconditioner(lqcd_ctx* c, lqcd_net* net)
 {
     if (!c) return fail(LQCD_ERR_INVALID, "null context");
     c->precond = net;
+    if (net) c->sap_on = 0;
     return LQCD_OK;
 }
 

@@ -1,5 +1,5 @@
 // Flexible GCR(k) on the full Wilson-clover operator with a right
-// preconditioner (identity or the parallel-transport network).
+// preconditioner (identity, SAP or the parallel-transport network).
 //
 // The paper's outer solver is FGCR: it stores two vectors per iteration
 // (z_k and w_k = M z_k), so it is restarted, and it tolerates a
@@ -207,6 +207,8 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     const double bn2 = h[SC_TMP + 0];
     const int block = 256;
     const dim3 grid(gcr_grid(c, block));
+    bool sap = !net && c->sap_on;
+    if (sap) LQ_TRY(sap_check(c, c->sap_bs));
     int iters = 0, restarts = 0, fallback = 0;
     double res = 1.0, res_prev = 0.0;
     lqcd_status status = LQCD_OK;
@@ -226,8 +228,9 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         if (log) fprintf(stderr, "[lqcd] fgcr iter %d restart, true residual %.3e\n", iters, res);
         if (!std::isfinite(res)) { status = LQCD_ERR_BREAKDOWN; break; }
         if (res <= tol) break;
-        // safeguard: a preconditioner that does not halve the residual over a
-        // whole cycle is replaced by the identity for the rest of the solve
+        // safeguard: a network that does not halve the residual over a whole
+        // cycle is replaced by the identity for the rest of the solve (SAP is
+        // a fixed convergent splitting and is kept)
         if (net && restarts > 0 && res > 0.5 * res_prev) {
             net = nullptr;
             fallback = 1;
@@ -242,6 +245,8 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
             char* zk = Zb + (size_t)k * fld;
             char* wk = Wb + (size_t)k * fld;
             if (net) LQ_TRY(net_apply_internal(net, zk, R32, fld));
+            else if (sap) LQ_TRY(sap_apply(c, zk, R32, c->sap_bs, c->sap_ncycle, c->sap_nmr, vec64_field(c, 4, 0),
+                                           vec64_field(c, 5, 0)));
             else LQ_TRY(convert_field(c, zk, P32, R32, P32, 1, fld, fld, 2, -1));
             LQ_TRY(op_full(c, wk, zk, mode, false, 1, fld));
             for (int pass = 0; pass < 2 && k > 0; ++pass) {

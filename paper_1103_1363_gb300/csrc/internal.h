@@ -61,7 +61,9 @@ struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 
 struct lqcd_ctx {
     lqcd::Profiler* prof;    // null unless lqcd_profile_enable was called
-    lqcd_net* precond;       // FGCR right preconditioner (null: identity)
+    lqcd_net* precond;       // FGCR right preconditioner (null: identity or SAP)
+    int sap_on;              // FGCR right preconditioner is SAP (sap_bs, sap_ncycle, sap_nmr)
+    int sap_bs[4], sap_ncycle, sap_nmr;
     lqcd_config cfg;
     lqcd::Geom g;
     cudaStream_t stream;
@@ -166,6 +168,11 @@ lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int nrhs,
 lqcd_status solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b, const double* tol,
                         const lqcd_solver_params* p, lqcd_solver_stats* st);
 // fgcr.cu
+// sap.cu: z = SAP(r) on FP32 full internal fields; rho_buf and dlt_buf are
+// two FP32 full fields of scratch (block residuals and corrections)
+lqcd_status sap_check(const lqcd_ctx* c, const int bs[4]);
+lqcd_status sap_apply(lqcd_ctx* c, void* z, const void* r, const int bs[4], int ncycle, int nmr, char* rho_buf,
+                      char* dlt_buf);
 lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, double tol,
                        const lqcd_solver_params* p, lqcd_solver_stats* st, bool host_io);
 

@@ -86,6 +86,8 @@ _SIGS = {
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
+    "lqcd_set_preconditioner_sap": [_P, _P, _I, _I],
+    "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
     "lqcd_tune": [_P, _I, C.POINTER(C.c_int)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
@@ -270,6 +272,26 @@ def lqcd_solve_batch(ctxs, xs, bs, tols, params=None, raise_on_error=True):
     return rc, [s.as_dict() for s in st]
 
 
+def _block4(block):
+    if block is None:
+        return None
+    if len(block) != 4:
+        raise ValueError("block needs four extents")
+    return C.cast((C.c_int * 4)(*[int(b) for b in block]), C.c_void_p)
+
+
+def lqcd_set_preconditioner_sap(ctx, block, ncycle=1, nmr=4):
+    """SAP as the FGCR right preconditioner (block=None switches it off)."""
+    _check(_lib.lqcd_set_preconditioner_sap(ctx, _block4(block), int(ncycle), int(nmr)),
+           "lqcd_set_preconditioner_sap")
+
+
+def lqcd_sap_apply(ctx, z, r, block, ncycle=1, nmr=4):
+    """z = SAP(r) on internal FP32 full fields (device)."""
+    _check(_lib.lqcd_sap_apply(ctx, _ptr(z), _ptr(r), _block4(block), int(ncycle), int(nmr)),
+           "lqcd_sap_apply")
+
+
 def lqcd_tune(ctx, prec):
     """Autotune the hopping kernels' block size; returns (plain, dagger) choices."""
     best = (C.c_int * 2)()
@@ -437,6 +459,12 @@ class Lattice:
 
     def solve(self, x, b, tol=1e-10, nrhs=1, raise_on_error=True, **kw):
         return lqcd_solve(self.ctx, x, b, tol, nrhs, solver_params(**kw), raise_on_error)
+
+    def sap_apply(self, z, r, block, ncycle=1, nmr=4):
+        lqcd_sap_apply(self.ctx, z, r, block, ncycle, nmr)
+
+    def set_sap(self, block, ncycle=1, nmr=4):
+        lqcd_set_preconditioner_sap(self.ctx, block, ncycle, nmr)
 
     def sync(self):
         lqcd_sync(self.ctx)
