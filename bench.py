@@ -354,7 +354,7 @@ def run_sap_kernel(args, w):
     dims = w["dims"]
     V = int(np.prod(dims))
     block = tuple(int(b) for b in args.block.split("x"))
-    K = 16
+    K = 24
     stream = torch.cuda.Stream()
     lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16"), recon=12, gcr_nkrylov=K, stream=stream)
     lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
