@@ -6,12 +6,22 @@
 // preconditioner that is not a fixed operator; mixed precision is
 // iterative refinement, i.e. the recursion runs in single precision and the
 // residual is recomputed in double precision at each restart (Sec. 5).
+//
 // Here w_k is orthogonalised against the earlier w_j by classical
-// Gram-Schmidt applied twice (the same coefficients update z_k), which in
-// exact arithmetic gives the same iterates as modified Gram-Schmidt but
-// needs two fused launches per pass instead of 2k.
+// Gram-Schmidt: one kernel forms <w_j, w_k>, <w_k, r> and |w_k|^2, the host
+// forms c_j = <w_j, w_k>/|w_j|^2 and the step a = <w_k, r>/|w^_k|^2 with
+// |w^_k|^2 = |w_k|^2 - sum_j |<w_j, w_k>|^2/|w_j|^2, and one fused kernel
+// writes w^_k = w_k - sum_j c_j w_j and r -= a w^_k.  When that estimate
+// shows cancellation (|w^_k|^2 < |w_k|^2 / 2, the "twice is enough"
+// criterion of Daniel, Gragg, Kaufman and Stewart) a second pass runs first.
+// r is orthogonal to the earlier w^_j, so <w^_k, r> = <w_k, r>.  The z_k are
+// not orthogonalised: with U the unit upper triangle of the coefficients
+// c_jk, the cycle's correction is x += Z U^{-1} a, formed once at the end of
+// the cycle.  In exact arithmetic these are the iterates of GCR with
+// modified Gram-Schmidt on both w and z.
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -23,20 +33,22 @@ namespace lqcd {
 
 lqcd_status net_apply_internal(lqcd_net* n, void* z, const void* r, size_t rb);
 
-enum { GCR_KMAX = 24 };
+enum { GCR_KMAX = 24, GCR_NDOT = 2 * GCR_KMAX + 3 };
 
-// dots[j] = <w_j, v> (j < k), complex, FP64 accumulation.
-__global__ void gcr_multidot_kernel(Geom g, const char* W, size_t fld, int k, const char* v, double* partials,
-                                    unsigned* ticket, double* out)
+// out[2j, 2j+1] = <w_j, w_k> (j < k), out[2k, 2k+1] = <w_k, r>,
+// out[2k+2] = |w_k|^2.  FP32 sums per thread, FP64 across threads.
+__global__ void gcr_dots_kernel(Geom g, const char* W, size_t fld, int k, const char* wk, const char* r,
+                                double* partials, unsigned* ticket, double* out)
 {
-    double acc[2 * GCR_KMAX];
+    float acc[GCR_NDOT];
 #pragma unroll
-    for (int j = 0; j < 2 * GCR_KMAX; ++j) acc[j] = 0.0;
+    for (int j = 0; j < GCR_NDOT; ++j) acc[j] = 0.f;
     const size_t fb = fld / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
         for (int par = 0; par < 2; ++par) {
-            float vv[24];
-            SpinorIO<P32>::load(v + par * fb, g.stride, i, vv);
+            float vv[24], rv[24];
+            SpinorIO<P32>::load(wk + par * fb, g.stride, i, vv);
+            SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
 #pragma unroll
             for (int j = 0; j < GCR_KMAX; ++j) {
                 if (j >= k) break;
@@ -51,96 +63,96 @@ __global__ void gcr_multidot_kernel(Geom g, const char* W, size_t fld, int k, co
                 acc[2 * j] += re;
                 acc[2 * j + 1] += im;
             }
+            float re = 0.f, im = 0.f, nn = 0.f;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                re += vv[2 * q] * rv[2 * q] + vv[2 * q + 1] * rv[2 * q + 1];
+                im += vv[2 * q] * rv[2 * q + 1] - vv[2 * q + 1] * rv[2 * q];
+                nn += vv[2 * q] * vv[2 * q] + vv[2 * q + 1] * vv[2 * q + 1];
+            }
+            acc[2 * GCR_KMAX] += re;
+            acc[2 * GCR_KMAX + 1] += im;
+            acc[2 * GCR_KMAX + 2] += nn;
         }
-    block_reduce_finalize<2 * GCR_KMAX>(acc, partials, ticket, out);
+    double d[GCR_NDOT];
+#pragma unroll
+    for (int j = 0; j < GCR_NDOT; ++j) d[j] = acc[j];
+    block_reduce_finalize<GCR_NDOT>(d, partials, ticket, out);
 }
 
-// w_k -= sum_j c_j w_j, z_k -= sum_j c_j z_j with c_j = dots[j] / wnorm[j].
-__global__ void gcr_multiaxpy_kernel(Geom g, const char* W, const char* Z, size_t fld, int k, char* wk, char* zk,
-                                     const double* dots, const double* wnorm)
+struct GcrStep {
+    float2 c[GCR_KMAX];  // w_k -= sum_j c_j w_j
+    float2 a;            // r -= a w_k (after the projection)
+    int update_r;
+};
+
+// w_k -= sum_j c_j w_j; if update_r: r -= a w_k.  out[0] = |r|^2, out[1] = |w_k|^2.
+__global__ void gcr_orth_update_kernel(Geom g, const char* W, size_t fld, int k, char* wk, char* r, GcrStep st,
+                                       double* partials, unsigned* ticket, double* out)
 {
-    __shared__ float cr[GCR_KMAX], ci[GCR_KMAX];
-    if (threadIdx.x < k) {
-        cr[threadIdx.x] = (float)(dots[2 * threadIdx.x] / wnorm[threadIdx.x]);
-        ci[threadIdx.x] = (float)(dots[2 * threadIdx.x + 1] / wnorm[threadIdx.x]);
-    }
-    __syncthreads();
+    double acc[2] = {0.0, 0.0};
     const size_t fb = fld / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
         for (int par = 0; par < 2; ++par) {
-            float a[24], b[24];
+            float a[24];
             SpinorIO<P32>::load(wk + par * fb, g.stride, i, a);
-            SpinorIO<P32>::load(zk + par * fb, g.stride, i, b);
             for (int j = 0; j < k; ++j) {
-                float w[24], z[24];
+                float w[24];
                 SpinorIO<P32>::load(W + j * fld + par * fb, g.stride, i, w);
-                SpinorIO<P32>::load(Z + j * fld + par * fb, g.stride, i, z);
-                const float xr = cr[j], xi = ci[j];
+                const float xr = st.c[j].x, xi = st.c[j].y;
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
                     a[2 * q] -= xr * w[2 * q] - xi * w[2 * q + 1];
                     a[2 * q + 1] -= xr * w[2 * q + 1] + xi * w[2 * q];
-                    b[2 * q] -= xr * z[2 * q] - xi * z[2 * q + 1];
-                    b[2 * q + 1] -= xr * z[2 * q + 1] + xi * z[2 * q];
                 }
             }
-            SpinorIO<P32>::store(wk + par * fb, g.stride, i, a);
-            SpinorIO<P32>::store(zk + par * fb, g.stride, i, b);
+            if (k > 0) SpinorIO<P32>::store(wk + par * fb, g.stride, i, a);
+            float nw = 0.f, nr = 0.f;
+#pragma unroll
+            for (int q = 0; q < 24; ++q) nw += a[q] * a[q];
+            if (st.update_r) {
+                float rv[24];
+                SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    rv[2 * q] -= st.a.x * a[2 * q] - st.a.y * a[2 * q + 1];
+                    rv[2 * q + 1] -= st.a.x * a[2 * q + 1] + st.a.y * a[2 * q];
+                }
+                SpinorIO<P32>::store(r + par * fb, g.stride, i, rv);
+#pragma unroll
+                for (int q = 0; q < 24; ++q) nr += rv[q] * rv[q];
+            }
+            acc[0] += nr;
+            acc[1] += nw;
         }
+    block_reduce_finalize<2>(acc, partials, ticket, out);
 }
 
-// out[0..1] = <w, r>, out[2] = |w|^2
-__global__ void gcr_dot3_kernel(Geom g, const char* w, const char* r, size_t fb, double* partials, unsigned* ticket,
-                                double* out)
-{
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
-        for (int par = 0; par < 2; ++par) {
-            float a[24], b[24];
-            SpinorIO<P32>::load(w + par * fb, g.stride, i, a);
-            SpinorIO<P32>::load(r + par * fb, g.stride, i, b);
-            float re = 0.f, im = 0.f, nn = 0.f;
-#pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                re += a[2 * q] * b[2 * q] + a[2 * q + 1] * b[2 * q + 1];
-                im += a[2 * q] * b[2 * q + 1] - a[2 * q + 1] * b[2 * q];
-                nn += a[2 * q] * a[2 * q] + a[2 * q + 1] * a[2 * q + 1];
-            }
-            acc[0] += re;
-            acc[1] += im;
-            acc[2] += nn;
-        }
-    block_reduce_finalize<3>(acc, partials, ticket, out);
-}
+struct GcrCombine {
+    float2 beta[GCR_KMAX];
+};
 
-// x += a z, r -= a w with a = d3[0..1] / d3[2]; |r|^2 -> out; wnorm_k = d3[2]
-__global__ void gcr_update_kernel(Geom g, char* x, char* r, const char* z, const char* w, size_t fb, const double* d3,
-                                  double* wnorm_k, double* partials, unsigned* ticket, double* out)
+// x = sum_{k < m} beta_k z_k
+__global__ void gcr_combine_kernel(Geom g, const char* Z, size_t fld, int m, GcrCombine cb, char* x)
 {
-    const float ar = (float)(d3[0] / d3[2]), ai = (float)(d3[1] / d3[2]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *wnorm_k = d3[2];
-    double acc[1] = {0.0};
+    const size_t fb = fld / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
         for (int par = 0; par < 2; ++par) {
-            float xv[24], rv[24], zv[24], wv[24];
-            SpinorIO<P32>::load(x + par * fb, g.stride, i, xv);
-            SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
-            SpinorIO<P32>::load(z + par * fb, g.stride, i, zv);
-            SpinorIO<P32>::load(w + par * fb, g.stride, i, wv);
-            float nn = 0.f;
+            float a[24];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                xv[2 * q] += ar * zv[2 * q] - ai * zv[2 * q + 1];
-                xv[2 * q + 1] += ar * zv[2 * q + 1] + ai * zv[2 * q];
-                rv[2 * q] -= ar * wv[2 * q] - ai * wv[2 * q + 1];
-                rv[2 * q + 1] -= ar * wv[2 * q + 1] + ai * wv[2 * q];
-                nn += rv[2 * q] * rv[2 * q] + rv[2 * q + 1] * rv[2 * q + 1];
+            for (int q = 0; q < 24; ++q) a[q] = 0.f;
+            for (int k = 0; k < m; ++k) {
+                float z[24];
+                SpinorIO<P32>::load(Z + k * fld + par * fb, g.stride, i, z);
+                const float br = cb.beta[k].x, bi = cb.beta[k].y;
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    a[2 * q] += br * z[2 * q] - bi * z[2 * q + 1];
+                    a[2 * q + 1] += br * z[2 * q + 1] + bi * z[2 * q];
+                }
             }
-            acc[0] += nn;
-            SpinorIO<P32>::store(x + par * fb, g.stride, i, xv);
-            SpinorIO<P32>::store(r + par * fb, g.stride, i, rv);
+            SpinorIO<P32>::store(x + par * fb, g.stride, i, a);
         }
-    block_reduce_finalize<1>(acc, partials, ticket, out);
 }
 
 namespace {
@@ -177,11 +189,9 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     char* R32 = Wb + (size_t)K * fld;
     char* X32 = R32 + fld;
     double* dev = reinterpret_cast<double*>(X32 + fld);  // scalars of the recursion
-    double* dots = dev;                                    // [2 GCR_KMAX]
-    double* wnorm = dev + 2 * GCR_KMAX;                    // [GCR_KMAX]
-    double* d3 = wnorm + GCR_KMAX;                         // [3]
-    double* rr = d3 + 4;                                   // [1]
-    unsigned* tick = reinterpret_cast<unsigned*>(rr + 4);  // [1]
+    double* dots = dev;                                    // [GCR_NDOT]
+    double* upd = dev + 64;                                // [2]
+    unsigned* tick = reinterpret_cast<unsigned*>(upd + 4); // [1]
     double* parts = reinterpret_cast<double*>(reinterpret_cast<char*>(tick) + 256);
     const size_t canon_rb = (size_t)c->volume * 192;
 
@@ -212,6 +222,27 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     int iters = 0, restarts = 0, fallback = 0;
     double res = 1.0, res_prev = 0.0;
     lqcd_status status = LQCD_OK;
+    typedef std::complex<double> cd;
+    std::vector<cd> alpha(K), coef((size_t)K * K);  // coef[j * K + k] = c_jk
+    std::vector<double> wn(K);                       // |w^_j|^2
+    std::vector<double> hd(GCR_NDOT);
+    auto launch_dots = [&](int k, const char* wk) -> lqcd_status {
+        gcr_dots_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, parts, tick, dots);
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+        return read(dots, hd.data(), GCR_NDOT);
+    };
+    auto launch_update = [&](int k, char* wk, const cd* cj, cd a, bool update_r, double out[2]) -> lqcd_status {
+        GcrStep st;
+        memset(&st, 0, sizeof st);
+        for (int j = 0; j < k; ++j) st.c[j] = make_float2((float)cj[j].real(), (float)cj[j].imag());
+        st.a = make_float2((float)a.real(), (float)a.imag());
+        st.update_r = update_r ? 1 : 0;
+        gcr_orth_update_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, st, parts, tick, upd);
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+        return read(upd, out, 2);
+    };
     while (true) {
         // restart: r = b - M x with FP64 accuracy; stop on the true residual,
         // confirmed with native FP64 arithmetic when double-float was used
@@ -240,7 +271,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         if (iters >= p->maxiter) { status = LQCD_ERR_NOT_CONVERGED; break; }
         restarts++;
         LQ_TRY(convert_field(c, R32, P32, T2, P64, 1, fld, rb64, 2, -1));
-        LQ_TRY(blas_zero(c, X32, P32, 1, fld, 2));
+        int m = 0;  // vectors of this cycle
         for (int k = 0; k < K && iters < p->maxiter; ++k) {
             char* zk = Zb + (size_t)k * fld;
             char* wk = Wb + (size_t)k * fld;
@@ -249,26 +280,55 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
                                            vec64_field(c, 5, 0)));
             else LQ_TRY(convert_field(c, zk, P32, R32, P32, 1, fld, fld, 2, -1));
             LQ_TRY(op_full(c, wk, zk, mode, false, 1, fld));
-            for (int pass = 0; pass < 2 && k > 0; ++pass) {
-                gcr_multidot_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, parts, tick, dots);
-                LQ_CUDA(cudaGetLastError());
-                gcr_multiaxpy_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, Zb, fld, k, wk, zk, dots, wnorm);
-                LQ_CUDA(cudaGetLastError());
-                c->launches += 2;
+            // classical Gram-Schmidt, a second pass when the first cancels
+            std::vector<cd> ck(k, cd(0.0, 0.0)), cj(k);
+            double out[2] = {0.0, 0.0};
+            cd a(0.0, 0.0);
+            double what2 = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                LQ_TRY(launch_dots(k, wk));
+                const double ww = hd[2 * GCR_KMAX + 2];
+                what2 = ww;
+                for (int j = 0; j < k; ++j) {
+                    const cd d(hd[2 * j], hd[2 * j + 1]);
+                    cj[j] = d / wn[j];
+                    what2 -= std::norm(d) / wn[j];
+                }
+                const cd wr(hd[2 * GCR_KMAX], hd[2 * GCR_KMAX + 1]);
+                if (!(ww > 0.0) || !std::isfinite(ww)) { what2 = 0.0; break; }
+                for (int j = 0; j < k; ++j) ck[j] += cj[j];
+                if (pass == 0 && k > 0 && what2 < 0.5 * ww) {
+                    LQ_TRY(launch_update(k, wk, cj.data(), cd(0.0, 0.0), false, out));
+                    continue;
+                }
+                a = wr / what2;
+                LQ_TRY(launch_update(k, wk, cj.data(), a, true, out));
+                break;
             }
-            gcr_dot3_kernel<<<grid, block, 0, c->stream>>>(c->g, wk, R32, fb, parts, tick, d3);
-            LQ_CUDA(cudaGetLastError());
-            gcr_update_kernel<<<grid, block, 0, c->stream>>>(c->g, X32, R32, zk, wk, fb, d3, wnorm + k, parts, tick, rr);
-            LQ_CUDA(cudaGetLastError());
-            c->launches += 2;
+            if (!(what2 > 0.0) || !std::isfinite(out[0])) { status = LQCD_ERR_BREAKDOWN; break; }
+            wn[k] = out[1];
+            alpha[k] = a;
+            for (int j = 0; j < k; ++j) coef[(size_t)j * K + k] = ck[j];
+            m = k + 1;
             ++iters;
-            double r2 = 0.0;
-            LQ_TRY(read(rr, &r2, 1));
+            const double r2 = out[0];
             if (log) fprintf(stderr, "[lqcd] fgcr iter %d |r|/|b| %.3e\n", iters, std::sqrt(r2 / bn2));
-            if (!std::isfinite(r2)) { status = LQCD_ERR_BREAKDOWN; break; }
             if (std::sqrt(r2 / bn2) <= 0.5 * tol) break;
         }
         if (status != LQCD_OK) break;
+        // x += Z U^{-1} a: back substitution with the unit upper triangle
+        GcrCombine cb;
+        memset(&cb, 0, sizeof cb);
+        std::vector<cd> beta(m);
+        for (int k = m - 1; k >= 0; --k) {
+            cd v = alpha[k];
+            for (int j = k + 1; j < m; ++j) v -= coef[(size_t)k * K + j] * beta[j];
+            beta[k] = v;
+            cb.beta[k] = make_float2((float)v.real(), (float)v.imag());
+        }
+        gcr_combine_kernel<<<grid, block, 0, c->stream>>>(c->g, Zb, fld, m, cb, X32);
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
         LQ_TRY(blas_accumulate_x(c, X, X32, P32, 1, rb64, fld, 2));
     }
     // final true residual (recomputed above at the last restart check) and x
