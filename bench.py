@@ -45,6 +45,15 @@ WORKLOADS = {
 }
 TOL = 1e-10
 FALLBACK_HBM_GBS = 6800.0
+STORAGE = {
+    "f32": "f32 spinors, links (recon-12) and clover",
+    "f16": "f16 spinors (per-site norm), links (recon-12) and clover",
+    "bf16": "bf16 spinors (per-site norm), links (recon-12) and clover",
+    "f16links": "f16 links (recon-12) and clover, f32 spinors",
+    "bf16links": "bf16 links (recon-12) and clover, f32 spinors",
+    "f16spinors": "f16 spinors (per-site norm), f32 links (recon-12) and clover",
+    "bf16spinors": "bf16 spinors (per-site norm), f32 links (recon-12) and clover",
+}
 
 
 def workload_name(w):
@@ -158,7 +167,8 @@ def run_ours(args, w, rank, world, local_rank):
     t0 = time.time()
     lat.clover_compute(w["kappa"], w["csw"])
     clover_s = time.time() - t0
-    tuned = {p: lqcd.lqcd_tune(lat.ctx, p) for p in ("f64", args.inner)}  # block sizes (plain, dagger)
+    # block sizes (plain, plain reducing, dagger, dagger reducing)
+    tuned = {p: lqcd.lqcd_tune(lat.ctx, p) for p in ("f64", args.inner)}
     del Ud
     params = dict(inner_prec=args.inner, reliable_interval=50, check_interval=10)
 
@@ -195,7 +205,7 @@ def run_ours(args, w, rank, world, local_rank):
     worst_res = max(s["true_residual"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
 
-    # dominant kernel: the FP16 hopping kernels (all epilogues) inside the solve
+    # dominant kernel: the hopping kernels of the inner precision (all epilogues) inside the solve
     hb, hbsrc = measured_peaks()
     pf = prof[args.inner]
     achieved = pf["bytes"] / (pf["ms"] * 1e-3) / 1e9 if pf["ms"] > 0 else 0.0
@@ -247,6 +257,8 @@ def compare_solves(lat, bd, xd, stream, params):
                      ("bf16_inner_f64_ru", dict(params, inner_prec="bf16")),
                      ("f16links_inner_f64_ru", dict(params, inner_prec="f16links")),
                      ("bf16links_inner_f64_ru", dict(params, inner_prec="bf16links")),
+                     ("f16spinors_inner_f64_ru", dict(params, inner_prec="f16spinors")),
+                     ("bf16spinors_inner_f64_ru", dict(params, inner_prec="bf16spinors")),
                      ("f32_inner_f64_ru", dict(params, inner_prec="f32")),
                      ("plain_f64_cg", dict(inner_prec="f64", check_interval=10))):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -304,7 +316,7 @@ def run_hop_kernel(args, w):
     dims = w["dims"]
     Vh = int(np.prod(dims)) // 2
     stream = torch.cuda.Stream()
-    lat = lqcd.Lattice(dims, precisions=("f64", args.prec), recon=args.recon, stream=stream)
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, stream=stream)
     lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
     b = synth.gaussian_spinor(dims, w["src_seed"])
     nbuf = 8
@@ -323,8 +335,12 @@ def run_hop_kernel(args, w):
     e1.record(stream)
     stream.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / args.steps
-    sb = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52}[args.prec]
-    lb = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24}[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
+    spinor = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52, "f16links": 96, "bf16links": 96, "f16spinors": 52,
+              "bf16spinors": 52}
+    link = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24, "f16links": 24, "bf16links": 24, "f16spinors": 48,
+            "bf16spinors": 48}
+    sb = spinor[args.prec]
+    lb = link[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
     comp = (2 * sb + 8 * lb) * Vh
     hb, src = measured_peaks()
     print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "workload": workload_name(w),
@@ -465,7 +481,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32c64", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip the comparison legs (and the solves of --kernel sap)")
-    ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links"],
+    ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links", "f16spinors",
+                                                      "bf16spinors"],
                     help="storage of the timed solve's inner iteration")
     ap.add_argument("--kernel", default=None, choices=["hop", "sap"],
                     help="instead of the solve: time the stand-alone parity hopping kernel, or the SAP "
@@ -505,7 +522,7 @@ def main():
             "metric": METRIC, "value": round(r["value"], 2), "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "storage": "f16 spinors/links/clover with per-site norm; f64 reliable updates",
+            "storage": STORAGE[args.inner] + "; f64 reliable updates",
             "data": "synthetic",
             "config": {"workload": workload_name(w), "inner": args.inner, "reliable_update_every": 50,
                        "recon": 12, "parallelism": "replicas" if world > 1 else "single",

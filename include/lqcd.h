@@ -73,10 +73,12 @@ typedef enum {
 /* Storage precision of links, clover and spinor fields.  Arithmetic is FP64
  * for LQCD_F64 and FP32 for every other value.  LQCD_F16_LINKS and
  * LQCD_BF16_LINKS keep the operator's coefficients (links and clover) in
- * FP16 / BF16 but every spinor field in the F32 layout: rounding only the
- * coefficients perturbs the operator by a fixed Hermitian amount that CG
- * tolerates, while rounding the Krylov vectors to 11 (8) mantissa bits
- * injects noise that the operator amplifies by its condition number. */
+ * FP16 / BF16 and every spinor field in the F32 layout; LQCD_F16_SPINORS and
+ * LQCD_BF16_SPINORS the reverse: spinor fields in FP16 / BF16 with a per-site
+ * norm, links and clover in FP32.  Rounding the coefficients perturbs M by a
+ * fixed relative 2^-11 (2^-8), which CG on the normal equations feels through
+ * cond(Mhat^dag Mhat); rounding the vectors perturbs each iteration by the
+ * same relative amount without changing the operator. */
 typedef enum {
     LQCD_F64 = 0,
     LQCD_F32 = 1,
@@ -87,7 +89,9 @@ typedef enum {
     LQCD_F64_DF = 6,  /* FP64 storage and layout, arithmetic in pairs of FP32
                          (double-float, ~48-bit significand): FP64-accurate
                          operator applications at FP32 instruction rate */
-    LQCD_NPREC = 7
+    LQCD_F16_SPINORS = 7,   /* FP16 spinors (per-site norm), FP32 links and clover */
+    LQCD_BF16_SPINORS = 8,  /* BF16 spinors (per-site norm), FP32 links and clover */
+    LQCD_NPREC = 9
 } lqcd_prec;
 
 /* operator selection for lqcd_dslash (op_flags) */
@@ -308,12 +312,15 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 
 /* Autotuner: time the hopping kernels of precision `prec` (plain and dagger,
- * x-pay epilogue as in the solvers) at 32, 64, 96 and 128 threads per block
- * on this context's lattice and keep the fastest for every later launch.
- * Needs a loaded gauge field; overwrites the solver vectors of the
- * workspace.  best_block (may be NULL) receives the choice for plain [0]
- * and dagger [1].  Synchronises the stream. */
-lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[2]);
+ * x-pay epilogue as in the solvers, with and without the fused norm
+ * reduction) at 128, 96, 64 and 32 threads per block on this context's
+ * lattice and keep, for each of the four classes, the fastest (a smaller
+ * block must win by 2 %) for every later launch of that class: reducing
+ * launches (fused norms, fused CG updates) write one partial sum per block
+ * and are tuned apart from the plain ones.  Needs a loaded gauge field;
+ * overwrites the solver vectors of the workspace.  best_block (may be NULL)
+ * receives the choices [2 * dag + reducing].  Synchronises the stream. */
+lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[4]);
 
 /* Kernel timing.  While enabled, every hopping-term launch the context
  * issues is bracketed by CUDA events on its stream (graph replays are not

@@ -101,7 +101,7 @@ static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int 
 
 lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int epi, bool red, int nrhs)
 {
-    int block = c->tuned_block[P][dag ? 1 : 0];
+    int block = c->tuned_block[P][dag ? 1 : 0][red ? 1 : 0];
     if (block <= 0) block = c->block;
     const int rc = c->recon_of(mode_pg(P));
     Profiler* pr = c->prof;
@@ -124,6 +124,8 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int
     case PB16: e = dslash_dispatch_bf16(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case MODE_F16_LINKS: e = dslash_dispatch_f16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case MODE_BF16_LINKS: e = dslash_dispatch_bf16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    case MODE_F16_SPINORS: e = dslash_dispatch_f16spinors(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    case MODE_BF16_SPINORS: e = dslash_dispatch_bf16spinors(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     default: e = dslash_dispatch_df(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     }
     LQ_CUDA(e);
@@ -616,47 +618,54 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
     LQ_GUARD_END
 }
 
-lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[2])
+lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4])
 {
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     LQ_TRY(check_prec(c, prec));
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_tune: no gauge field loaded");
     LQ_TRY(set_device_of(c));
-    // scratch: two full fields of the FP64-sized solver vectors, zeroed
+    // scratch: two full fields of the FP64-sized solver vectors, filled with
+    // a non-zero byte pattern (finite in every storage format)
     const size_t fb = c->field_bytes(prec);
     char* in = vec64_field(c, 0, 0);
     char* out = vec64_field(c, 1, 0);
-    LQ_CUDA(cudaMemsetAsync(in, 0, 2 * fb, c->stream));
+    LQ_CUDA(cudaMemsetAsync(in, 0x3c, 2 * fb, c->stream));
     cudaEvent_t e0, e1;
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));
-    const int cands[4] = {32, 64, 96, 128};
+    const int cands[4] = {128, 96, 64, 32};  // the default first: it wins ties
     lqcd_status st = LQCD_OK;
-    for (int dag = 0; dag < 2 && st == LQCD_OK; ++dag) {
-        float best = 1e30f;
-        int best_b = DSLASH_MAX_BLOCK;
-        for (int ci = 0; ci < 4 && st == LQCD_OK; ++ci) {
-            c->tuned_block[prec][dag] = cands[ci];
-            float ms = 0.f;
-            for (int rep = 0; rep < 4 && st == LQCD_OK; ++rep) {  // rep 0 warms up
-                if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
-                if (st == LQCD_OK)
-                    st = op_hop(c, out + fb, in, 1, prec, dag != 0, EPI_XPAY, false, nullptr, in + fb, -0.1, 1, fb, -1);
-                if (st == LQCD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess)
-                    st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
-                if (st == LQCD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: sync");
-                float t = 0.f;
-                if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+    // reducing launches (fused norms and CG updates) write one partial sum
+    // per CTA, so they are tuned apart from the plain ones
+    for (int dag = 0; dag < 2 && st == LQCD_OK; ++dag)
+        for (int red = 0; red < 2 && st == LQCD_OK; ++red) {
+            float best = 1e30f;
+            int best_b = c->block;
+            for (int ci = 0; ci < 4 && st == LQCD_OK; ++ci) {
+                c->tuned_block[prec][dag][red] = cands[ci];
+                float ms = 0.f;
+                for (int rep = 0; rep < 6 && st == LQCD_OK; ++rep) {  // rep 0 warms up
+                    if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+                    if (st == LQCD_OK)
+                        st = op_hop(c, out + fb, in, 1, prec, dag != 0, EPI_XPAY, red != 0, nullptr, in + fb, -0.1, 1,
+                                    fb, red ? SC_TMP + 7 : -1);
+                    if (st == LQCD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess)
+                        st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+                    if (st == LQCD_OK && cudaEventSynchronize(e1) != cudaSuccess)
+                        st = fail(LQCD_ERR_CUDA, "lqcd_tune: sync");
+                    float t = 0.f;
+                    if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+                }
+                // a smaller block has to be faster by 2 % to replace the larger one
+                if (st == LQCD_OK && ms < 0.98f * best) {
+                    best = ms;
+                    best_b = cands[ci];
+                }
             }
-            if (st == LQCD_OK && ms < best) {
-                best = ms;
-                best_b = cands[ci];
-            }
+            c->tuned_block[prec][dag][red] = best_b;
+            if (best_block) best_block[2 * dag + red] = best_b;
         }
-        c->tuned_block[prec][dag] = best_b;
-        if (best_block) best_block[dag] = best_b;
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;

@@ -90,12 +90,30 @@ __host__ __device__ inline int AccumPrec(int P) { return P == P64 ? P64 : P32; }
 // BF16 and every spinor field in FP32.  The arithmetic is FP64 for mode 0
 // and FP32 otherwise.
 // Mode 6 stores everything in FP64 and computes in double-float.
-enum { MODE_F16_LINKS = 4, MODE_BF16_LINKS = 5, MODE_DF = 6, NMODES = 7 };
+enum { MODE_F16_LINKS = 4, MODE_BF16_LINKS = 5, MODE_DF = 6, MODE_F16_SPINORS = 7, MODE_BF16_SPINORS = 8,
+       NMODES = 9 };
 __host__ __device__ inline int mode_pg(int m)
 {
-    return m == MODE_F16_LINKS ? P16 : m == MODE_BF16_LINKS ? PB16 : m == MODE_DF ? P64 : m;
+    switch (m) {
+    case MODE_F16_LINKS: return P16;
+    case MODE_BF16_LINKS: return PB16;
+    case MODE_DF: return P64;
+    case MODE_F16_SPINORS:
+    case MODE_BF16_SPINORS: return P32;
+    default: return m;
+    }
 }
-__host__ __device__ inline int mode_ps(int m) { return m == MODE_DF ? P64 : m >= MODE_F16_LINKS ? P32 : m; }
+__host__ __device__ inline int mode_ps(int m)
+{
+    switch (m) {
+    case MODE_F16_LINKS:
+    case MODE_BF16_LINKS: return P32;
+    case MODE_DF: return P64;
+    case MODE_F16_SPINORS: return P16;
+    case MODE_BF16_SPINORS: return PB16;
+    default: return m;
+    }
+}
 
 // Lattice geometry of one context, passed by value to every kernel.
 struct Geom {

@@ -54,6 +54,8 @@ cudaError_t dslash_dispatch_bf16(const DslashArgs&, int, bool, int, bool, int, i
 cudaError_t dslash_dispatch_f16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_bf16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_df(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
+cudaError_t dslash_dispatch_f16spinors(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
+cudaError_t dslash_dispatch_bf16spinors(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 
 struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 
@@ -101,7 +103,8 @@ struct lqcd_ctx {
     int block;               // threads per block of the dslash kernels
     long dslash_count;
     long launches;           // kernels launched by this context (all kinds)
-    int tuned_block[lqcd::NMODES][2];  // per precision mode, dag: tuned block size (0 = default)
+    // tuned threads per block: [precision mode][dag][launch reduces into a scalar] (0 = default)
+    int tuned_block[lqcd::NMODES][2][2];
 
     // bytes of one single-parity spinor field of precision mode m
     size_t field_bytes(int m) const { return lqcd::spinor_field_bytes(lqcd::mode_ps(m), g.stride); }

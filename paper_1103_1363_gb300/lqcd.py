@@ -28,12 +28,13 @@ _lib = C.CDLL(LIB_PATH)
 LQCD_OK = 0
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_STATE",
           5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_CLOVER_SINGULAR"}
-F64, F32, F16, BF16, F16_LINKS, BF16_LINKS, F64_DF = 0, 1, 2, 3, 4, 5, 6
+F64, F32, F16, BF16, F16_LINKS, BF16_LINKS, F64_DF, F16_SPINORS, BF16_SPINORS = range(9)
 PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "f16links": F16_LINKS,
-        "bf16links": BF16_LINKS, "f64df": F64_DF}
-PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df")
+        "bf16links": BF16_LINKS, "f64df": F64_DF, "f16spinors": F16_SPINORS, "bf16spinors": BF16_SPINORS}
+PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df", "f16spinors", "bf16spinors")
 # storage precision of links / clover for each mode (the bit it needs in prec_mask)
-_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16, F64_DF: F64}
+_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16, F64_DF: F64,
+            F16_SPINORS: F32, BF16_SPINORS: F32}
 OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
 SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR = 0, 1, 2
 
@@ -293,10 +294,11 @@ def lqcd_sap_apply(ctx, z, r, block, ncycle=1, nmr=4):
 
 
 def lqcd_tune(ctx, prec):
-    """Autotune the hopping kernels' block size; returns (plain, dagger) choices."""
-    best = (C.c_int * 2)()
+    """Autotune the hopping kernels' block size; returns the choices
+    (plain, plain reducing, dagger, dagger reducing)."""
+    best = (C.c_int * 4)()
     _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best), "lqcd_tune")
-    return best[0], best[1]
+    return tuple(best)
 
 
 def lqcd_profile_enable(ctx, enable=True):

@@ -46,7 +46,7 @@ def test_cgnr_fp64_4444(lq):
         st["iterations"], it, res, st["true_residual"]))
 
 
-@pytest.mark.parametrize("inner", ["bf16", "bf16links", "f16"])
+@pytest.mark.parametrize("inner", ["bf16", "bf16links", "f16", "bf16spinors"])
 def test_eo_cg_bf16_16c16(lq, inner):
     """BF16 storage (8 mantissa bits) converges on the 16^4 system of the
     32^3x64 ensemble (exp(0.4 i H), kappa 0.1355) but needs several times the
@@ -66,7 +66,7 @@ def test_eo_cg_bf16_16c16(lq, inner):
     print("16^4 %s: %d iters, res %.2e" % (inner, st["iterations"], res))
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "f16links"])
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "f16links", "f16spinors"])
 def test_eo_cg_clover(lq, inner):
     dims = (8, 8, 8, 8)
     kappa, csw = 0.13, 1.0
