@@ -4,8 +4,11 @@
 Workload (synthetic, seeded): 32^3 x 64 lattice, links exp(i 0.4 H) (gauge
 seed 3), kappa 0.1355, csw 1.0 (four-leaf clover), Gaussian source (seed 0),
 antiperiodic t; mixed-precision even-odd CG on the normal equations: FP16
-storage with per-site norms and FP32 arithmetic inside, FP64 reliable
-update every 50 iterations, stopped at true residual |b - M x|/|b| <= 1e-10.
+spinor storage with per-site norms, FP32 links (recon-12) and clover, FP32
+arithmetic inside, FP64 reliable update every 50 iterations, stopped at true
+residual |b - M x|/|b| <= 1e-10.  (With the links and clover in FP16 too the
+operator's rounding, amplified by the condition number of the normal
+equations, triples the iteration count; that variant is timed as well.)
 
 One step = one complete solve (b and the solution resident in HBM; the
 gauge field and the clover term are set up beforehand).  The metric is the
@@ -13,7 +16,7 @@ sustained dslash rate of the solve: hopping applications x 1320 flops x V/2
 sites / wall time.  Also reported: the dslash kernels' achieved HBM
 bandwidth against the measured copy bandwidth (roofline), the end-to-end
 rate through lqcd_solve with host buffers, solve times of the plain FP64
-CG and the FP32 / BF16-inner solves on the same system, a stand-alone FP32
+CG and of every other inner storage on the same system, a stand-alone FP32
 recon-12 dslash rate, and the FP64 CPU oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -481,7 +484,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32c64", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip the comparison legs (and the solves of --kernel sap)")
-    ap.add_argument("--inner", default="f16", choices=["f32", "f16", "bf16", "f16links", "bf16links", "f16spinors",
+    ap.add_argument("--inner", default="f16spinors", choices=["f32", "f16", "bf16", "f16links", "bf16links", "f16spinors",
                                                       "bf16spinors"],
                     help="storage of the timed solve's inner iteration")
     ap.add_argument("--kernel", default=None, choices=["hop", "sap"],

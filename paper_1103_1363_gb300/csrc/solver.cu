@@ -172,16 +172,34 @@ lqcd_status true_system_residual(Cg& s)
     return LQCD_OK;
 }
 
+// RV_o = Mhat^dag d_o for an FP64 odd field d (stride rb64), |RV_o|^2 into
+// slot.  Only the defect d needs FP64 (it comes from a cancellation); the
+// map applied to it does not, so a mixed solve with FP32 links at hand
+// applies Mhat^dag in FP32 to d rounded to FP32, which is as accurate as
+// rounding the FP64 product into the FP32 vector.  T1 is the scratch.
+lqcd_status normal_residual_eo(Cg& s, const char* d_odd, int slot)
+{
+    lqcd_ctx* c = s.c;
+    if (s.PA == P32 && c->holds(P32)) {
+        char* d32 = s.T1;                         // R fields at stride rba
+        char* tmp = s.T1 + (size_t)s.R * s.rba;   // R even scratch fields
+        LQ_TRY(convert_field(c, d32, P32, d_odd, P64, s.R, s.rba, s.rb64, 1, -1));
+        return op_schur(c, s.RV + s.fba, d32, tmp, LQCD_F32, true, s.R, s.rba, s.rba, slot);
+    }
+    LQ_TRY(op_schur(c, s.RH + s.fb64, d_odd, s.T1, s.Pres, true, s.R, s.rb64, s.rb64, -1));
+    return convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, s.R, s.rba, s.rb64, 1, slot);
+}
+
 // Reliable update at block slot j: fold x, recompute r = K^dag (bhat - K x_hi)
-// in FP64, replace the inner r and its norm in slot j.
+// with the defect bhat - K x_hi in FP64, replace the inner r and its norm in
+// slot j.
 lqcd_status reliable_update(Cg& s, int j)
 {
     lqcd_ctx* c = s.c;
     LQ_TRY(fold_x(s));
     LQ_TRY(true_system_residual(s));
     if (s.eo) {
-        LQ_TRY(op_schur(c, s.RH + s.fb64, s.T2 + s.fb64, s.T1, s.Pres, true, s.R, s.rb64, s.rb64, -1));
-        LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, s.R, s.rba, s.rb64, 1, rr_slot(j) + 1));
+        LQ_TRY(normal_residual_eo(s, s.T2 + s.fb64, rr_slot(j) + 1));
     } else {
         LQ_TRY(op_full(c, s.RH, s.T2, s.Pres, true, s.R, s.rb64));
         LQ_TRY(convert_field(c, s.RV, s.PA, s.RH, P64, s.R, s.rba, s.rb64, 1, rr_slot(j)));
@@ -332,8 +350,7 @@ lqcd_status cg_setup(CgRun& run, lqcd_ctx* c, double* x, const double* b, double
         LQ_TRY(op_hop(c, s.BH + s.fb64, src_e, 1, P64, false, EPI_XPAY, false, nullptr, s.B + s.fb64, c->kappa, R,
                       s.rb64, -1));
         // r0 = Mhat^dag bhat_o (x0 = 0)
-        LQ_TRY(op_schur(c, s.RH + s.fb64, s.BH + s.fb64, s.T2, P64, true, R, s.rb64, s.rb64, -1));
-        LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, R, s.rba, s.rb64, 1, rr_slot(0) + 1));
+        LQ_TRY(normal_residual_eo(s, s.BH + s.fb64, rr_slot(0) + 1));
         LQ_TRY(convert_field(c, s.Pv + s.fbi, mode_ps(s.Pi), s.RV + s.fba, s.PA, R, s.rbi, s.rba, 1, -1));
     } else {
         LQ_TRY(op_full(c, s.RH, s.B, P64, true, R, s.rb64));
