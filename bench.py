@@ -48,6 +48,11 @@ WORKLOADS = {
 }
 TOL = 1e-10
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per output site of the inner hopping kernels,
+# from one ncu capture of a CG iteration on 24^3x48 (the four launches of an
+# iteration: Mhat sweeps with A^-1 and x-pay + norm epilogues, Mhat^dag sweeps
+# with A^-1 and the fused CG update); traffic grows with the sites processed.
+DRAM_BYTES_PER_SITE = {"f16spinors": (766.0 + 819.0 + 767.0 + 1152.0) / 4}
 STORAGE = {
     "f32": "f32 spinors, links (recon-12) and clover",
     "f16": "f16 spinors (per-site norm), links (recon-12) and clover",
@@ -219,6 +224,11 @@ def run_ours(args, w, rank, world, local_rank):
                 "launches": pf["launches"], "avg_launch_us": round(1e3 * pf["ms"] / max(1, pf["launches"]), 2),
                 "kernel_time_share": round(sum(p["ms"] for p in prof.values()) / (ms / world if world > 1 else ms), 4),
                 "traffic": None}
+    if args.inner in DRAM_BYTES_PER_SITE:
+        roofline["traffic"] = round(DRAM_BYTES_PER_SITE[args.inner] * Vh)
+        roofline["traffic_note"] = ("bytes per launch: ncu dram read+write per output site on 24^3x48, mean over the "
+                                    "four launches of an iteration, times V/2; algorithmic bytes per launch here %d"
+                                    % round(pf["bytes"] / max(1, pf["launches"])))
 
     out = {"value": value, "ms": ms, "stats": stats, "roofline": roofline, "clocks": clk,
            "dslash_total": dslash_total, "worst_res": worst_res, "launches": launches,
