@@ -19,6 +19,12 @@
 // c_jk, the cycle's correction is x += Z U^{-1} a, formed once at the end of
 // the cycle.  In exact arithmetic these are the iterates of GCR with
 // modified Gram-Schmidt on both w and z.
+//
+// A cycle ends (FP64 residual, restart) after nkrylov directions, or once
+// the FP32 residual has fallen by GCR_CYCLE_REDUCTION from the cycle's start,
+// or when a new direction lies numerically in the span of the earlier ones:
+// past FP32's resolution of the starting residual the recursion only adds
+// rounding, and the rebuilt solution would no longer match it.
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -34,6 +40,7 @@ namespace lqcd {
 lqcd_status net_apply_internal(lqcd_net* n, void* z, const void* r, size_t rb);
 
 enum { GCR_KMAX = 24, GCR_NDOT = 2 * GCR_KMAX + 3 };
+constexpr double GCR_CYCLE_REDUCTION = 1e-5;
 
 // out[2j, 2j+1] = <w_j, w_k> (j < k), out[2k, 2k+1] = <w_k, r>,
 // out[2k+2] = |w_k|^2.  FP32 sums per thread, FP64 across threads.
@@ -271,6 +278,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         if (iters >= p->maxiter) { status = LQCD_ERR_NOT_CONVERGED; break; }
         restarts++;
         LQ_TRY(convert_field(c, R32, P32, T2, P64, 1, fld, rb64, 2, -1));
+        const double r2_cycle = h[SC_TMP + 2];  // |r|^2 at the restart
         int m = 0;  // vectors of this cycle
         for (int k = 0; k < K && iters < p->maxiter; ++k) {
             char* zk = Zb + (size_t)k * fld;
@@ -284,10 +292,12 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
             std::vector<cd> ck(k, cd(0.0, 0.0)), cj(k);
             double out[2] = {0.0, 0.0};
             cd a(0.0, 0.0);
-            double what2 = 0.0;
+            double what2 = 0.0, ww0 = 0.0;
+            bool used = false;
             for (int pass = 0; pass < 2; ++pass) {
                 LQ_TRY(launch_dots(k, wk));
                 const double ww = hd[2 * GCR_KMAX + 2];
+                if (pass == 0) ww0 = ww;
                 what2 = ww;
                 for (int j = 0; j < k; ++j) {
                     const cd d(hd[2 * j], hd[2 * j + 1]);
@@ -295,7 +305,8 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
                     what2 -= std::norm(d) / wn[j];
                 }
                 const cd wr(hd[2 * GCR_KMAX], hd[2 * GCR_KMAX + 1]);
-                if (!(ww > 0.0) || !std::isfinite(ww)) { what2 = 0.0; break; }
+                // nothing new in w_k (also catches NaN): do not use it
+                if (!(what2 > 1e-10 * ww0) || !std::isfinite(ww)) break;
                 for (int j = 0; j < k; ++j) ck[j] += cj[j];
                 if (pass == 0 && k > 0 && what2 < 0.5 * ww) {
                     LQ_TRY(launch_update(k, wk, cj.data(), cd(0.0, 0.0), false, out));
@@ -303,9 +314,15 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
                 }
                 a = wr / what2;
                 LQ_TRY(launch_update(k, wk, cj.data(), a, true, out));
+                used = true;
                 break;
             }
-            if (!(what2 > 0.0) || !std::isfinite(out[0])) { status = LQCD_ERR_BREAKDOWN; break; }
+            if (!used) {
+                // w_k lies in the span of the earlier w_j: end the cycle without it
+                if (k == 0) status = LQCD_ERR_BREAKDOWN;
+                break;
+            }
+            if (!std::isfinite(out[0])) { status = LQCD_ERR_BREAKDOWN; break; }
             wn[k] = out[1];
             alpha[k] = a;
             for (int j = 0; j < k; ++j) coef[(size_t)j * K + k] = ck[j];
@@ -314,6 +331,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
             const double r2 = out[0];
             if (log) fprintf(stderr, "[lqcd] fgcr iter %d |r|/|b| %.3e\n", iters, std::sqrt(r2 / bn2));
             if (std::sqrt(r2 / bn2) <= 0.5 * tol) break;
+            if (r2 <= GCR_CYCLE_REDUCTION * GCR_CYCLE_REDUCTION * r2_cycle) break;
         }
         if (status != LQCD_OK) break;
         // x += Z U^{-1} a: back substitution with the unit upper triangle

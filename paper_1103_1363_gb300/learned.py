@@ -141,11 +141,13 @@ def eo_cg_solve(lat, b, tol=1e-10, inner="f32"):
 
 def run_experiment(dims=(16, 16, 16, 16), eps=0.5, kappa=0.134, csw=1.0, train_seeds=range(100, 124),
                    test_seeds=range(124, 132), npairs=4096, channels=(1, 12, 12, 1), epochs=10, batch=16,
-                   lr=1e-3, net_seed=7, device="cuda", log=print):
+                   lr=1e-3, net_seed=7, device="cuda", log=print, sap_block=(4, 4, 4, 4), sap_ncycle=5,
+                   sap_nmr=4):
     """The learned-preconditioner workload: train on pairs from the training
     fields, then solve one Gaussian source per held-out field with FGCR(20)
-    + trained net, FGCR(20) + untrained net, FGCR(20) + identity and
-    mixed-precision even-odd CG, all to true residual 1e-10."""
+    + trained net, FGCR(20) + untrained net, FGCR(20) + identity, FGCR(20) +
+    SAP (the paper's preconditioner in the same slot) and mixed-precision
+    even-odd CG (FP32 and FP16-spinor inner), all to true residual 1e-10."""
     import synth
     lat = lqcd.Lattice(dims, precisions=("f64", "f32"), max_nrhs=64, gcr_nkrylov=20, device=device)
     train_seeds, test_seeds = list(train_seeds), list(test_seeds)
@@ -184,13 +186,18 @@ def run_experiment(dims=(16, 16, 16, 16), eps=0.5, kappa=0.134, csw=1.0, train_s
         net.set_weights(w_trained)
         _, row["fgcr_trained"] = fgcr_solve(lat, b)
         net.use_as_preconditioner(False)
+        if sap_block is not None:
+            lat.set_sap(sap_block, sap_ncycle, sap_nmr)
+            _, row["fgcr_sap"] = fgcr_solve(lat, b)
+            lat.set_sap(None)
         _, row["eo_cg_f32"] = eo_cg_solve(lat, b)
+        _, row["eo_cg_f16spinors"] = eo_cg_solve(lat, b, inner="f16spinors")
         results.append(row)
         log("test %d: " % s + ", ".join("%s %d it %.3f s res %.1e" % (k, v["iterations"], v["wall_s"],
                                                                        v["true_residual"])
                                         for k, v in row.items() if k != "seed"))
     summary = {}
-    for k in ("fgcr_identity", "fgcr_untrained", "fgcr_trained", "eo_cg_f32"):
+    for k in [k for k in results[0] if k != "seed"]:
         summary[k] = {"iterations_mean": float(np.mean([r[k]["iterations"] for r in results])),
                       "wall_s_mean": float(np.mean([r[k]["wall_s"] for r in results])),
                       "true_residual_max": float(max(r[k]["true_residual"] for r in results)),

@@ -114,3 +114,28 @@ def test_fgcr_with_sap(lq):
     assert st["iterations"] < st_id["iterations"]
     assert abs(st["iterations"] - it_o) <= max(3, it_o // 8)
     lat.set_sap(None)
+
+
+def test_fgcr_with_strong_sap_restarts_in_time(lq):
+    """5 SAP cycles leave ~4e-3 of the residual per application, so the FP32
+    recursion reaches FP32's resolution of the cycle's starting residual
+    within a few iterations; the cycle must then end and restart from the
+    FP64 residual (8^4, kappa 0.13: this diverged when the cycle ran on)."""
+    dims, block = (8, 8, 8, 8), (4, 4, 4, 4)
+    kappa, csw = 0.13, 1.0
+    U = synth.smooth_gauge(dims, 0.5, 124)
+    A = oracle.clover(U, kappa, csw)
+    b = synth.gaussian_spinor(dims, 1124)
+    lat = lq.Lattice(dims, gcr_nkrylov=20)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    bt = torch.from_numpy(b).cuda()
+    for ncycle in (3, 5, 8):
+        lat.set_sap(block, ncycle=ncycle, nmr=4)
+        x = lat.canonical_spinor()
+        rc, st = lat.solve(x, bt, 1e-10, solver=lq.SOLVER_FGCR, inner_prec="f32", nkrylov=20, maxiter=400)
+        res = oracle.true_residual(U, A, kappa, b, x.cpu().numpy())
+        print("SAP ncycle %d: %d iterations, %d restarts, res %.2e" % (ncycle, st["iterations"], st["restarts"], res))
+        assert rc == 0 and res <= 1e-10
+        assert st["iterations"] <= 30
+    lat.set_sap(None)
