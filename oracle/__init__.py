@@ -320,3 +320,21 @@ def fgcr(U, A, kappa, b, tol=1e-10, nkrylov=20, maxiter=100000, prec=None, tanti
     st = lib().oracle_fgcr(_dims(dims_of(U)), tanti, _p(U), _Aptr(A), kappa, _p(b), _p(x), tol,
                            nkrylov, maxiter, cb, None, C.byref(it), C.byref(res))
     return x, it.value, res.value, st == 0
+
+
+def fgmres_dr(U, A, kappa, b, tol=1e-10, m=20, k=0, maxiter=100000, prec=None, tanti=1, history=None,
+              on_restart=None):
+    """Flexible GMRES(m) with k deflated vectors at restarts on M (Sec. 7;
+    oracle/fgmresdr.py).  prec(r) -> z on canonical arrays (None: identity).
+    Returns (x, iterations, true relative residual, converged)."""
+    from . import fgmresdr
+    U = _c(U)
+    A = None if A is None else _c(A)
+    shape = b.shape
+
+    def matvec(v):
+        return wilson_clover(U, A, kappa, v.reshape(shape), tanti=tanti).reshape(-1)
+
+    p = None if prec is None else (lambda v: np.asarray(prec(v.reshape(shape)), dtype=complex).reshape(-1))
+    x, it, res, ok = fgmresdr.fgmres_dr(matvec, b, tol, m, k, maxiter, p, history, on_restart)
+    return x.reshape(shape), it, res, ok
