@@ -162,7 +162,10 @@ lqcd_status lqcd_clover_apply(lqcd_ctx* ctx, void* out, const void* in, int pari
 typedef enum {
     LQCD_SOLVER_CG_EO = 0,   /* CG on Mhat^dag Mhat (even-odd), reconstruct x_e */
     LQCD_SOLVER_CG_FULL = 1, /* CG on M^dag M over the full lattice (CGNR) */
-    LQCD_SOLVER_FGCR = 2     /* flexible GCR(nkrylov) on M, right preconditioned */
+    LQCD_SOLVER_FGCR = 2,    /* flexible GCR(nkrylov) on M, right preconditioned */
+    LQCD_SOLVER_FGMRES_DR = 3 /* flexible GMRES on M with a Krylov space of nkrylov
+                                 vectors, ndefl of them kept at each restart
+                                 (deflated restart, Sec. 7); right preconditioned */
 } lqcd_solver_kind;
 
 typedef struct {
@@ -179,6 +182,8 @@ typedef struct {
                                 residuals of a mixed solve (an FP64 inner solve always
                                 uses LQCD_F64); the final reported residual is always
                                 native FP64 */
+    int ndefl;               /* FGMRES-DR: harmonic Ritz vectors kept at a restart
+                                (0 <= ndefl <= 16, < nkrylov; 0: plain restarted FGMRES) */
 } lqcd_solver_params;
 
 typedef struct {
@@ -195,7 +200,13 @@ typedef struct {
 } lqcd_solver_stats;
 
 /* Defaults: CG_EO, F32 inner, maxiter 100000, reliable every 50, delta 0.1,
- * check every 10, nkrylov 20, no graph. */
+ * check every 10, nkrylov 20, no graph, ndefl 0.
+ *
+ * LQCD_SOLVER_FGCR and LQCD_SOLVER_FGMRES_DR run their recursion on FP32
+ * full fields (inner_prec F32, F16_LINKS or BF16_LINKS for the operator) and
+ * recompute the residual b - M x in FP64 at every restart; they need
+ * cfg.gcr_nkrylov >= nkrylov.  FGCR allows nkrylov <= 24, FGMRES-DR
+ * nkrylov <= cfg.gcr_nkrylov. */
 lqcd_status lqcd_solver_params_default(lqcd_solver_params* p);
 
 /* Solve M x = b for nrhs canonical FP64 right-hand sides (host or device
@@ -269,8 +280,8 @@ lqcd_status lqcd_net_forward(lqcd_net* net, float* out, const float* in, int bat
 lqcd_status lqcd_net_train_step(lqcd_net* net, const float* r, const float* e, int batch, double lr, double beta1,
                                 double beta2, double eps, double* loss);
 
-/* Right preconditioner of LQCD_SOLVER_FGCR (NULL: identity, i.e. plain
- * GCR).  The network must belong to this context and outlive its use. */
+/* Right preconditioner of LQCD_SOLVER_FGCR and LQCD_SOLVER_FGMRES_DR (NULL:
+ * identity).  The network must belong to this context and outlive its use. */
 lqcd_status lqcd_set_preconditioner(lqcd_ctx* ctx, lqcd_net* net);
 
 /* Schwarz alternating procedure (Sec. 5, the SAP preconditioner of the
@@ -307,6 +318,16 @@ lqcd_status lqcd_sap_apply(lqcd_ctx* ctx, void* z, const void* r, const int bloc
  * tol[i] (stats[i]).  Returns the first non-OK status of the lattices. */
 lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b,
                              const double* tol, const lqcd_solver_params* params, lqcd_solver_stats* stats);
+
+/* The deflation step of FGMRES-DR (Sec. 7, deflated restart), host only:
+ * for M Z = V Hbar with Hbar of nz + 1 rows and nz columns (complex,
+ * column-major, leading dimension ldh >= nz + 1, interleaved re/im
+ * doubles), the k harmonic Ritz pairs of smallest |theta|, i.e. solutions
+ * of Hbar^H Hbar g = theta Hsq^H g with Hsq the leading nz x nz block.
+ * theta: k complex (2k doubles); g: nz x k complex, column-major, unit
+ * columns.  1 <= k <= nz <= 256.  LQCD_ERR_BREAKDOWN if Hsq is singular or
+ * the eigenvalue iteration does not converge.  Needs no GPU. */
+lqcd_status lqcd_harmonic_ritz(int nz, const double* hbar, int ldh, int k, double* theta, double* g);
 
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);

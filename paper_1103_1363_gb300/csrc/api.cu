@@ -306,7 +306,10 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     take(c->s_veclo, (size_t)NVLO * R * full64);
     take(c->s_vecacc, (size_t)NVACC * R * full64);
     // FGCR: z_0..z_{k-1}, w_0..w_{k-1}, r, x (FP32 full fields) + scalars and reduction partials
-    c->gcr_bytes = cfg->gcr_nkrylov > 0 ? (size_t)(2 * cfg->gcr_nkrylov + 2) * 2 * c->field_bytes(P32) + (256 << 10) : 0;
+    // FGCR: 2K + 2 FP32 full fields; FGMRES-DR: V (K + 1), Z (K), r, x: 2K + 3;
+    // then the scalars of the recursions (reduction partials, coefficients)
+    c->gcr_bytes = cfg->gcr_nkrylov > 0 ? (size_t)(2 * cfg->gcr_nkrylov + 3) * 2 * c->field_bytes(P32) + GCR_SCALAR_BYTES
+                                        : 0;
     take(c->s_gcr, c->gcr_bytes);
     c->need = off;
     *out = c;
@@ -691,6 +694,7 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
     p->check_interval = 10;
     p->nkrylov = 20;
     p->use_graph = 0;
+    p->ndefl = 0;
     // native FP64: the double-float kernels measured slower on GB300 (255
     // registers, one 4-warp block per SM, dependent FP32 chains)
     p->residual_prec = LQCD_F64;

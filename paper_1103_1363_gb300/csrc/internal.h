@@ -120,6 +120,10 @@ struct lqcd_ctx {
 
 namespace lqcd {
 
+// bytes after the FP32 fields of the FGCR / FGMRES-DR region: reduction
+// partials, dot products and coefficient arrays of the recursions
+enum : size_t { GCR_SCALAR_BYTES = (size_t)4 << 20 };
+
 // number of full (both-parity) FP64 fields per rhs in vec64
 enum { NV64 = 6 };
 // inner-precision full fields per rhs in veclo
@@ -178,5 +182,8 @@ lqcd_status sap_apply(lqcd_ctx* c, void* z, const void* r, const int bs[4], int 
                       char* dlt_buf);
 lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, double tol,
                        const lqcd_solver_params* p, lqcd_solver_stats* st, bool host_io);
+// fgmres.cu
+lqcd_status solve_fgmres_dr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, double tol,
+                            const lqcd_solver_params* p, lqcd_solver_stats* st, bool host_io);
 
 }  // namespace lqcd

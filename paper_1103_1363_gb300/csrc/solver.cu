@@ -592,10 +592,11 @@ lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
 lqcd_status solve(lqcd_ctx* c, double* x, const double* b, double tol, int R, const lqcd_solver_params* p,
                   lqcd_solver_stats* st)
 {
-    if (p->solver == LQCD_SOLVER_FGCR) {
-        if (R != 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR solves one right-hand side per call");
+    if (p->solver == LQCD_SOLVER_FGCR || p->solver == LQCD_SOLVER_FGMRES_DR) {
+        if (R != 1) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR / FGMRES-DR solve one right-hand side per call");
         const bool hio = !is_device(b);
         if (hio != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");
+        if (p->solver == LQCD_SOLVER_FGMRES_DR) return solve_fgmres_dr(c, c->precond, x, b, tol, p, st, hio);
         return solve_fgcr(c, c->precond, x, b, tol, p, st, hio);
     }
     CgRun run;

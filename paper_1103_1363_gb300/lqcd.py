@@ -36,7 +36,7 @@ PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df", "f1
 _STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16, F64_DF: F64,
             F16_SPINORS: F32, BF16_SPINORS: F32}
 OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
-SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR = 0, 1, 2
+SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR, SOLVER_FGMRES_DR = 0, 1, 2, 3
 
 
 class lqcd_config(C.Structure):
@@ -48,7 +48,7 @@ class lqcd_solver_params(C.Structure):
     _fields_ = [("solver", C.c_int), ("inner_prec", C.c_int), ("maxiter", C.c_int),
                 ("reliable_interval", C.c_int), ("reliable_delta", C.c_double),
                 ("check_interval", C.c_int), ("nkrylov", C.c_int), ("use_graph", C.c_int),
-                ("residual_prec", C.c_int)]
+                ("residual_prec", C.c_int), ("ndefl", C.c_int)]
 
 
 class lqcd_solver_stats(C.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
     "lqcd_set_preconditioner_sap": [_P, _P, _I, _I],
+    "lqcd_harmonic_ritz": [_I, _P, _I, _I, _P, _P],
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
     "lqcd_tune": [_P, _I, C.POINTER(C.c_int)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
@@ -271,6 +272,18 @@ def lqcd_solve_batch(ctxs, xs, bs, tols, params=None, raise_on_error=True):
     if raise_on_error:
         _check(rc, "lqcd_solve_batch")
     return rc, [s.as_dict() for s in st]
+
+
+def lqcd_harmonic_ritz(hbar, nz, k):
+    """Harmonic Ritz pairs of FGMRES-DR's deflation step (host, no GPU):
+    hbar complex (nz + 1, nz); returns (theta[k], g[nz, k])."""
+    # column-major storage = the C-contiguous transpose
+    ht = np.ascontiguousarray(np.asarray(hbar, dtype=np.complex128)[:nz + 1, :nz].T)
+    theta = np.zeros(k, dtype=np.complex128)
+    gt = np.zeros((k, nz), dtype=np.complex128)
+    _check(_lib.lqcd_harmonic_ritz(int(nz), _ptr(ht), int(nz + 1), int(k), _ptr(theta), _ptr(gt)),
+           "lqcd_harmonic_ritz")
+    return theta, gt.T
 
 
 def _block4(block):
