@@ -374,8 +374,9 @@ def sap_block_flops(block):
 
 def run_sap_kernel(args, w):
     """SAP on the workload's lattice: the application z = SAP(r) alone
-    (rotating buffers, larger than L2), then SAP-FGCR against identity-FGCR
-    and the FP16-inner even-odd CG to the same tolerance."""
+    (rotating buffers, larger than L2), then SAP-FGCR(24), SAP-FGMRES-DR
+    (70 vectors, 10 deflated) and SAP-FGMRES(70) against identity-FGCR and
+    the even-odd CG (FP16-spinor and all-FP16 inner) to the same tolerance."""
     import torch
 
     import synth
@@ -384,8 +385,9 @@ def run_sap_kernel(args, w):
     V = int(np.prod(dims))
     block = tuple(int(b) for b in args.block.split("x"))
     K = 24
+    MDR, KDR = 70, 10  # FGMRES-DR: Krylov space of 70 with 10 deflated vectors, as in Sec. 7
     stream = torch.cuda.Stream()
-    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16"), recon=12, gcr_nkrylov=K, stream=stream)
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", "f16"), recon=12, gcr_nkrylov=MDR, stream=stream)
     lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
     lat.clover_compute(w["kappa"], w["csw"])
     b = synth.gaussian_spinor(dims, w["src_seed"])
@@ -417,12 +419,22 @@ def run_sap_kernel(args, w):
     xd = lat.canonical_spinor()
     solves = {}
     for name, sap, kw in (("fgcr_sap", True, dict(solver=lqcd.SOLVER_FGCR, inner_prec="f32", nkrylov=K)),
+                          ("fgmres_dr_sap", True, dict(solver=lqcd.SOLVER_FGMRES_DR, inner_prec="f32", nkrylov=MDR,
+                                                       ndefl=KDR)),
+                          ("fgmres_sap", True, dict(solver=lqcd.SOLVER_FGMRES_DR, inner_prec="f32", nkrylov=MDR,
+                                                    ndefl=0)),
+                          ("eo_cg_f16spinors_inner", False, dict(inner_prec="f16spinors", reliable_interval=50,
+                                                                 check_interval=10)),
                           ("eo_cg_f16_inner", False, dict(inner_prec="f16", reliable_interval=50,
                                                           check_interval=10)),
                           ("fgcr_identity", False, dict(solver=lqcd.SOLVER_FGCR, inner_prec="f32", nkrylov=K,
-                                                        maxiter=20000))):
+                                                        maxiter=20000)),
+                          ("fgmres_dr_identity", False, dict(solver=lqcd.SOLVER_FGMRES_DR, inner_prec="f32",
+                                                             nkrylov=MDR, ndefl=KDR, maxiter=20000)),
+                          ("fgmres_identity", False, dict(solver=lqcd.SOLVER_FGMRES_DR, inner_prec="f32", nkrylov=MDR,
+                                                          ndefl=0, maxiter=20000))):
         lat.set_sap(block if sap else None, args.ncycle, args.nmr)
-        if name != "fgcr_identity":
+        if not name.endswith("_identity"):
             lat.solve(xd, bd, TOL, raise_on_error=False, **kw)  # warm-up (graphs, first-touch)
         stream.synchronize()
         e0.record(stream)

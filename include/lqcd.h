@@ -108,7 +108,8 @@ typedef struct {
     int recon;            /* 12 or 18: link storage for F32/F16/BF16 (F64 always 18) */
     int prec_mask;        /* bit (1 << lqcd_prec) for each precision to hold; F64 is always held */
     int max_nrhs;         /* largest nrhs used with the solver vectors (>= 1) */
-    int gcr_nkrylov;      /* Krylov space of FGCR (0: no FGCR vectors reserved) */
+    int gcr_nkrylov;      /* Krylov space of FGCR / FGMRES-DR, 0..256 (0: no vectors
+                             reserved; 2 gcr_nkrylov + 3 FP32 full fields otherwise) */
 } lqcd_config;
 
 /* Create a context for one lattice.  `cuda_stream` is a cudaStream_t (may

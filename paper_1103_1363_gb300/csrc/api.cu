@@ -256,7 +256,8 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     if (V / 2 > (1L << 30)) return fail(LQCD_ERR_INVALID, "lqcd_create: lattice too large");
     if (cfg->recon != 12 && cfg->recon != 18) return fail(LQCD_ERR_INVALID, "lqcd_create: recon must be 12 or 18");
     if (cfg->max_nrhs < 1 || cfg->max_nrhs > 64) return fail(LQCD_ERR_INVALID, "lqcd_create: max_nrhs must be in [1, 64]");
-    if (cfg->gcr_nkrylov < 0 || cfg->gcr_nkrylov > 64) return fail(LQCD_ERR_INVALID, "lqcd_create: gcr_nkrylov must be in [0, 64]");
+    if (cfg->gcr_nkrylov < 0 || cfg->gcr_nkrylov > 256)
+        return fail(LQCD_ERR_INVALID, "lqcd_create: gcr_nkrylov must be in [0, 256]");
     lqcd_ctx* c = new lqcd_ctx();
     memset(c, 0, sizeof(*c));
     c->cfg = *cfg;
