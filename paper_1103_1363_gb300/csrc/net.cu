@@ -90,32 +90,50 @@ __device__ __forceinline__ uint16_t f2bf(float f)
 }
 
 // Gather the transported inputs of hop h for the tile into shared memory:
-// X[row = site*3 + a][k2]; rows past V are zero.
+// X[row = site*3 + a][k2]; rows past V are zero.  The tile's links and
+// neighbours for the hop are staged once; then consecutive threads take
+// consecutive (channel, spin) pieces of the same neighbour, whose
+// activations are contiguous, so each warp reads one stretch of memory.
 template <int RECON, bool TC>
 __device__ __forceinline__ void gather_hop(const NetLayerArgs& a, const float* in_b, int tile0, int h, void* Xs,
                                            int xstride)
 {
+    __shared__ float us[NET_TS][19];  // link (18 floats) and fermion sign per site of the tile
+    __shared__ int ys[NET_TS];        // neighbour site, -1 past the lattice
     const int tid = threadIdx.x;
-    const int sl = tid % NET_TS;           // site in tile
-    const int kg = tid / NET_TS;           // 4 groups of k
-    const int x = tile0 + sl;
+    if (tid < NET_TS) {
+        const int x = tile0 + tid;
+        float u[18];
+        float sign = 1.f;
+        int y = -1;
+        if (x < a.V) {
+            y = hop_link<RECON>(a, x, h, u, sign);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) u[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 18; ++q) us[tid][q] = u[q];
+        us[tid][18] = sign;
+        ys[tid] = y;
+    }
+    __syncthreads();
     const int nk = 4 * a.cin;
-    float u[18];
-    float sign = 1.f;
-    int y = x;
-    const bool live = x < a.V;
-    if (live) y = hop_link<RECON>(a, x, h, u, sign);
-    for (int k = kg; k < a.K2p / 2; k += NET_THREADS / NET_TS) {
+    const int kp = a.K2p / 2;
+    for (int e = tid; e < NET_TS * kp; e += NET_THREADS) {
+        const int sl = e / kp, k = e - sl * kp;
+        const int y = ys[sl];
         float o[6] = {0, 0, 0, 0, 0, 0};
-        if (live && k < nk) {
+        if (y >= 0 && k < nk) {
             const float2* src = reinterpret_cast<const float2*>(in_b) + ((size_t)y * nk + k) * 3;
             const float2 p0 = src[0], p1 = src[1], p2 = src[2];
             if (h == 0) {
                 o[0] = p0.x; o[1] = p0.y; o[2] = p1.x; o[3] = p1.y; o[4] = p2.x; o[5] = p2.y;
             } else {
+                const float sign = us[sl][18];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    const float* ur = u + 6 * r;
+                    const float* ur = &us[sl][6 * r];
                     o[2 * r] = sign * (ur[0] * p0.x - ur[1] * p0.y + ur[2] * p1.x - ur[3] * p1.y + ur[4] * p2.x - ur[5] * p2.y);
                     o[2 * r + 1] = sign * (ur[0] * p0.y + ur[1] * p0.x + ur[2] * p1.y + ur[3] * p1.x + ur[4] * p2.y + ur[5] * p2.x);
                 }
