@@ -283,7 +283,8 @@ def compare_solves(lat, bd, xd, stream, params):
         stream.synchronize()
         res[name] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "iterations": st["iterations"],
                      "reliable_updates": st["reliable_updates"], "dslash": st["dslash_count"],
-                     "true_residual": st["true_residual"], "status": rc}
+                     "true_residual": st["true_residual"], "status": rc,
+                     "precision_fallback": st["precision_fallback"]}
     f64 = res["plain_f64_cg"]["seconds"]
     for k in res:
         res[k]["speedup_vs_f64_cg"] = round(f64 / res[k]["seconds"], 2)

@@ -198,6 +198,9 @@ typedef struct {
     int preconditioner_fallback; /* FGCR: 1 if the preconditioner stagnated (a restart
                                     cycle did not halve the residual) and the solve
                                     finished with the identity */
+    int precision_fallback;  /* CG with a 16-bit inner precision: 1 if three reliable
+                                updates in a row failed to halve |r|^2 and the solve
+                                finished with FP32 inner storage */
 } lqcd_solver_stats;
 
 /* Defaults: CG_EO, F32 inner, maxiter 100000, reliable every 50, delta 0.1,

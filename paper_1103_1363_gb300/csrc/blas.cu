@@ -74,7 +74,8 @@ __global__ void cg_p_kernel(Geom g, char* p, size_t p_rb, const char* r, size_t 
     const int rhs = blockIdx.y;
     if (skip && skip[rhs]) return;
     const double* sc = scal + rhs * SC_PER_RHS;
-    const RR beta = (RR)((sc[num] + sc[num + 1]) / (sc[den] + sc[den + 1]));
+    const double bden = sc[den] + sc[den + 1];  // 0 once the residual has vanished
+    const RR beta = bden > 0.0 ? (RR)((sc[num] + sc[num + 1]) / bden) : (RR)0;
     const size_t fp = spinor_field_bytes(PP, g.stride), fr = spinor_field_bytes(PR, g.stride);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
         for (int f = 0; f < nf; ++f) {

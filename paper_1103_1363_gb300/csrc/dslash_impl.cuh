@@ -341,7 +341,10 @@ __global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 
         if constexpr (EPI == EPI_CG) {
             typedef typename RealT<AccumP<PS>::value>::type RA;
             const double* sc = A.scal + rhs * A.scal_rs;
-            const RA alpha = (RA)((sc[A.s_num] + sc[A.s_num2]) / (sc[A.s_den] + sc[A.s_den2]));
+            // alpha = |r|^2 / |Mp|^2; once r is exactly zero (an exact solution
+            // inside a check interval) both vanish: no step instead of 0/0
+            const double den = sc[A.s_den] + sc[A.s_den2];
+            const RA alpha = den > 0.0 ? (RA)((sc[A.s_num] + sc[A.s_num2]) / den) : (RA)0;
             R pv[24];
             RA xv[24], rv[24];
             SpinorIO<PS>::load(static_cast<const char*>(A.p) + rhs * A.p_rb, A.g.stride, i, pv);

@@ -361,6 +361,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     st->kernel_launches = c->launches;
     st->true_residual = res;
     st->preconditioner_fallback = fallback;
+    st->precision_fallback = 0;
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (status == LQCD_ERR_NOT_CONVERGED) return fail(status, "lqcd_solve: FGCR not converged within maxiter");
     if (status == LQCD_ERR_BREAKDOWN) return fail(status, "lqcd_solve: FGCR breakdown");

@@ -265,6 +265,11 @@ struct CgRun {
     std::vector<int> done;
     bool mixed = false, log = false, ru_next = false;
     int ru_every = 0;
+    // stagnation of a 16-bit inner iteration: |r|^2 at consecutive reliable
+    // updates; after three that do not halve it the inner storage becomes FP32
+    std::vector<double> rr_last_ru;
+    int stalls = 0;
+    bool fell_back = false, rebuild_graphs = false;
     double delta2 = 0.0;
     int k = 0, since_ru = 0, nrestart = 0;
     lqcd_status status = LQCD_OK;
@@ -363,6 +368,7 @@ lqcd_status cg_setup(CgRun& run, lqcd_ctx* c, double* x, const double* b, double
     run.rr0.assign(R, 0.0);
     run.target.assign(R, 0.0);
     run.rrmax.assign(R, 0.0);
+    run.rr_last_ru.assign(R, 0.0);
     run.done.assign(R, 0);
     for (int r = 0; r < R; ++r) {
         run.bn2[r] = run.h[r * SC_PER_RHS + SC_TMP + 0];
@@ -380,6 +386,29 @@ lqcd_status cg_setup(CgRun& run, lqcd_ctx* c, double* x, const double* b, double
 
 // After a block of n iterations: read |r|^2, detect breakdown, check
 // candidates on the FP64 true residual, mark converged right-hand sides.
+// A 16-bit inner iteration that has stopped making progress between
+// reliable updates (on ill-conditioned systems 11 or 8 bits of the search
+// directions cannot resolve the remaining residual) continues with FP32
+// inner storage: the same links (FP32 copy), p restarted from r.
+lqcd_status fall_back_to_f32(CgRun& run)
+{
+    lqcd_ctx* c = run.c;
+    Cg& s = run.s;
+    run.stalls = 0;
+    if (run.fell_back || s.Pi == P64 || s.Pi == LQCD_F32 || mode_ps(s.Pi) == P64 || !c->holds(P32)) return LQCD_OK;
+    if (run.log) fprintf(stderr, "[lqcd] iter %d: inner iteration stagnates, continuing with FP32 storage\n", run.k);
+    s.Pi = LQCD_F32;
+    s.fbi = c->field_bytes(s.Pi);
+    s.rbi = 2 * s.fbi;
+    s.Qv = c->veclo + (size_t)s.R * s.rbi;
+    s.oi = s.eo ? s.fbi : 0;
+    if (s.eo) LQ_TRY(convert_field(c, s.Pv + s.fbi, P32, s.RV + s.fba, s.PA, s.R, s.rbi, s.rba, 1, -1));
+    else LQ_TRY(convert_field(c, s.Pv, P32, s.RV, s.PA, s.R, s.rbi, s.rba, 2, -1));
+    run.fell_back = true;
+    run.rebuild_graphs = true;
+    return LQCD_OK;
+}
+
 lqcd_status cg_check(CgRun& run, int n, bool ru)
 {
     lqcd_ctx* c = run.c;
@@ -393,7 +422,7 @@ lqcd_status cg_check(CgRun& run, int n, bool ru)
     }
     run.k += n;
     LQ_TRY(read_scalars(c, R, run.h));
-    bool any_candidate = false;
+    bool any_candidate = false, any_stall = false;
     for (int r = 0; r < R; ++r) {
         if (run.done[r]) continue;
         const double rr = run.h[r * SC_PER_RHS + rr_slot(0)] + run.h[r * SC_PER_RHS + rr_slot(0) + 1];
@@ -407,10 +436,18 @@ lqcd_status cg_check(CgRun& run, int n, bool ru)
             run.status = fail(LQCD_ERR_BREAKDOWN, msg);
             return run.status;
         }
-        if (ru) run.rrmax[r] = rr;
+        if (ru) {
+            run.rrmax[r] = rr;
+            if (run.rr_last_ru[r] > 0.0 && rr > 0.5 * run.rr_last_ru[r]) any_stall = true;
+            run.rr_last_ru[r] = rr;
+        }
         if (rr > run.rrmax[r]) run.rrmax[r] = rr;
         if (run.mixed && rr < run.delta2 * run.rrmax[r]) run.ru_next = true;
         if (rr <= run.target[r]) any_candidate = true;
+    }
+    if (ru) {
+        run.stalls = any_stall ? run.stalls + 1 : 0;
+        if (run.stalls >= 3) LQ_TRY(fall_back_to_f32(run));
     }
     if (!any_candidate) return LQCD_OK;
     // true residual of the full system for every rhs (x is folded, r untouched)
@@ -481,6 +518,7 @@ lqcd_status cg_finish(CgRun& run, lqcd_solver_stats* st)
     }
     st->iterations = run.k;
     st->reliable_updates = (int)s.reliable;
+    st->precision_fallback = run.fell_back ? 1 : 0;
     st->restarts = run.nrestart;
     st->dslash_count = c->dslash_count;
     st->kernel_launches = c->launches;
@@ -577,11 +615,15 @@ lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
                     if (bs != LQCD_OK) return bs;
                 }
         }
+        bool rebuild = false;
         for (size_t i = 0; i < runs.size(); ++i)
             if (mask >> i & 1) {
                 lqcd_status cs = cg_check(*runs[i], n, ru);
                 if (cs != LQCD_OK && runs[i]->status == LQCD_OK) { destroy_graphs(cache); return cs; }
+                rebuild = rebuild || runs[i]->rebuild_graphs;
+                runs[i]->rebuild_graphs = false;
             }
+        if (rebuild) destroy_graphs(cache);  // captured with the old inner precision
     }
     destroy_graphs(cache);
     return LQCD_OK;

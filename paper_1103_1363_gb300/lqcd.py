@@ -55,7 +55,7 @@ class lqcd_solver_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("reliable_updates", C.c_int), ("restarts", C.c_int),
                 ("dslash_count", C.c_long), ("kernel_launches", C.c_long),
                 ("true_residual", C.c_double), ("seconds", C.c_double),
-                ("preconditioner_fallback", C.c_int)]
+                ("preconditioner_fallback", C.c_int), ("precision_fallback", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,0 +1,88 @@
+"""Degenerate inputs of the solvers, through the C ABI on the GPU:
+
+- b = 0: every solver returns x = 0 exactly, with status OK and no
+  iteration (|b - M x| = 0 already).
+- b = M x* for a plane wave x* on a unit-link lattice without clover: the
+  Krylov space of b is one-dimensional for FGCR / FGMRES (M b is parallel
+  to b), so they converge in one iteration (the invariant-subspace case of
+  GMRES); CG on the normal equations reaches r = 0 after one iteration and
+  must survive the remaining iterations of its check interval (0/0 steps).
+- The smallest lattice (2^4, where x + mu and x - mu coincide) solves to
+  1e-10 with every solver, checked by the oracle.  Its rough Haar links make
+  the normal equations so ill-conditioned that 16-bit search directions
+  stagnate (|r|/|r0| ~ 2e-4); the CG then switches its inner storage to FP32
+  and says so in the stats.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_helpers import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+SOLVERS = [("cg_eo", dict(inner_prec="f32")), ("cg_eo_f16spinors", dict(inner_prec="f16spinors")),
+           ("cg_full", dict(solver=1, inner_prec="f32")), ("fgcr", dict(solver=2, inner_prec="f32", nkrylov=8)),
+           ("fgmres_dr", dict(solver=3, inner_prec="f32", nkrylov=8, ndefl=2))]
+
+
+@pytest.fixture(scope="module")
+def lq():
+    return require_cuda()
+
+
+@pytest.mark.parametrize("name,kw", SOLVERS, ids=[s[0] for s in SOLVERS])
+def test_zero_source(lq, name, kw):
+    dims = (4, 4, 4, 8)
+    lat = lq.Lattice(dims, gcr_nkrylov=8)
+    lat.gauge_load(synth.smooth_gauge(dims, 0.5, 71))
+    lat.clover_compute(0.13, 1.0)
+    x = lat.canonical_spinor()
+    x.fill_(7.0)
+    rc, st = lat.solve(x, torch.zeros_like(x), 1e-10, **kw)
+    assert rc == 0 and st["iterations"] == 0
+    assert not torch.any(x)
+
+
+@pytest.mark.parametrize("name,kw", SOLVERS, ids=[s[0] for s in SOLVERS])
+def test_plane_wave_source(lq, name, kw):
+    """Free field (unit links, csw 0, periodic in t): a plane wave of
+    momentum p with a fixed spinor u is an eigenvector of the hopping term
+    only if u is an eigenvector of the momentum's gamma combination; a zero
+    momentum wave is one for any u: H psi = 8 psi, M psi = (1 - 8 kappa) psi."""
+    dims = (4, 4, 4, 4)
+    kappa = 0.1
+    U = synth.unit_gauge(dims)
+    u = synth.gaussian_spinor((1, 1, 1, 1), 72)[0, 0, 0, 0]
+    xstar = np.broadcast_to(u, dims + (4, 3)).copy()
+    b = oracle.wilson_clover(U, None, kappa, xstar, tanti=0)
+    assert np.allclose(b, (1 - 8 * kappa) * xstar)
+    lat = lq.Lattice(dims, t_antiperiodic=0, gcr_nkrylov=8)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, 0.0)
+    x = lat.canonical_spinor()
+    rc, st = lat.solve(x, torch.from_numpy(b).cuda(), 1e-10, **kw)
+    xg = x.cpu().numpy()
+    assert rc == 0
+    assert np.linalg.norm(xg - xstar) / np.linalg.norm(xstar) < 1e-10
+    if name.startswith("fg"):  # CG checks its residual only every check_interval iterations
+        assert st["iterations"] <= 2, st["iterations"]
+
+
+@pytest.mark.parametrize("name,kw", SOLVERS, ids=[s[0] for s in SOLVERS])
+def test_smallest_lattice(lq, name, kw):
+    dims = (2, 2, 2, 2)
+    kappa, csw = 0.12, 1.0
+    U = synth.haar_gauge(dims, 73)
+    A = oracle.clover(U, kappa, csw)
+    b = synth.gaussian_spinor(dims, 74)
+    lat = lq.Lattice(dims, gcr_nkrylov=8)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    x = lat.canonical_spinor()
+    rc, st = lat.solve(x, torch.from_numpy(b).cuda(), 1e-10, **kw)
+    assert rc == 0
+    assert oracle.true_residual(U, A, kappa, b, x.cpu().numpy()) <= 1e-10
+    assert st["precision_fallback"] == (1 if "f16" in name else 0)
