@@ -232,7 +232,7 @@ def run_ours(args, w, rank, world, local_rank):
 
     out = {"value": value, "ms": ms, "stats": stats, "roofline": roofline, "clocks": clk,
            "dslash_total": dslash_total, "worst_res": worst_res, "launches": launches,
-           "clover_setup_s": round(clover_s, 3), "prof": prof, "tuned_block": tuned}
+           "clover_setup_s": round(clover_s, 3), "prof": prof, "tuned": tuned}
 
     if rank == 0 and not args.quick:
         out["e2e"] = e2e_leg(args, lat, b, Vh, params)
@@ -559,7 +559,7 @@ def main():
                                "reliable_updates": r["stats"][-1]["reliable_updates"],
                                "dslash": r["stats"][-1]["dslash_count"],
                                "true_residual_max": r["worst_res"]},
-            "clover_setup_s": r["clover_setup_s"], "tuned_block": r["tuned_block"],
+            "clover_setup_s": r["clover_setup_s"], "tuned": r["tuned"],
             "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"),
         }
         print(json.dumps(line), flush=True)

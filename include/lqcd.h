@@ -340,12 +340,16 @@ lqcd_status lqcd_sync(lqcd_ctx* ctx);
  * x-pay epilogue as in the solvers, with and without the fused norm
  * reduction) at 128, 96, 64 and 32 threads per block on this context's
  * lattice and keep, for each of the four classes, the fastest (a smaller
- * block must win by 2 %) for every later launch of that class: reducing
- * launches (fused norms, fused CG updates) write one partial sum per block
- * and are tuned apart from the plain ones.  Needs a loaded gauge field;
- * overwrites the solver vectors of the workspace.  best_block (may be NULL)
- * receives the choices [2 * dag + reducing].  Synchronises the stream. */
-lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[4]);
+ * block must win by 2 %) for every later launch of that class.  Reducing
+ * launches (fused norms, fused CG updates) write one partial sum per block:
+ * they are tuned apart from the plain ones, and for them also the sites each
+ * thread handles (one wave of resident blocks, the default, or 1, 4 or 16
+ * sites per thread; another choice must win by 2 %).  Needs a loaded gauge
+ * field; overwrites the solver vectors of the workspace.  best_block (may be
+ * NULL) receives the block sizes [2 * dag + reducing], best_sites (may be
+ * NULL) the sites per thread of the reducing launches [dag] (0: one wave).
+ * Synchronises the stream. */
+lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[4], int best_sites[2]);
 
 /* Kernel timing.  While enabled, every hopping-term launch the context
  * issues is bracketed by CUDA events on its stream (graph replays are not

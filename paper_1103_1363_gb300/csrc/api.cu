@@ -99,8 +99,10 @@ static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int 
     return b;
 }
 
-lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A, int P, bool dag, int epi, bool red, int nrhs)
+lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A0, int P, bool dag, int epi, bool red, int nrhs)
 {
+    DslashArgs A = A0;
+    if (red || epi == EPI_CG) A.sites_per_thread = c->tuned_spt[P][dag ? 1 : 0];
     int block = c->tuned_block[P][dag ? 1 : 0][red ? 1 : 0];
     if (block <= 0) block = c->block;
     const int rc = c->recon_of(mode_pg(P));
@@ -622,7 +624,7 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
     LQ_GUARD_END
 }
 
-lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4])
+lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_sites[2])
 {
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
@@ -638,29 +640,35 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4])
     cudaEvent_t e0, e1;
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));
-    const int cands[4] = {128, 96, 64, 32};  // the default first: it wins ties
     lqcd_status st = LQCD_OK;
-    // reducing launches (fused norms and CG updates) write one partial sum
-    // per CTA, so they are tuned apart from the plain ones
+    // time of 5 launches after one warm-up of the current setting
+    auto time_launches = [&](int dag, int red, float& ms) {
+        ms = 0.f;
+        for (int rep = 0; rep < 6 && st == LQCD_OK; ++rep) {  // rep 0 warms up
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+            if (st == LQCD_OK)
+                st = op_hop(c, out + fb, in, 1, prec, dag != 0, EPI_XPAY, red != 0, nullptr, in + fb, -0.1, 1, fb,
+                            red ? SC_TMP + 7 : -1);
+            if (st == LQCD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
+            if (st == LQCD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: sync");
+            float t = 0.f;
+            if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+        }
+    };
+    const int cands[4] = {128, 96, 64, 32};  // the default first: it wins ties
+    const int spts[4] = {0, 1, 4, 16};       // sites per thread of reducing launches (0: one wave of blocks)
+    // reducing launches (fused norms, fused CG updates) write one partial sum
+    // per block, so they are tuned apart from the plain ones, and for them
+    // the sites per thread as well
     for (int dag = 0; dag < 2 && st == LQCD_OK; ++dag)
         for (int red = 0; red < 2 && st == LQCD_OK; ++red) {
             float best = 1e30f;
             int best_b = c->block;
+            if (red) c->tuned_spt[prec][dag] = 0;
             for (int ci = 0; ci < 4 && st == LQCD_OK; ++ci) {
                 c->tuned_block[prec][dag][red] = cands[ci];
                 float ms = 0.f;
-                for (int rep = 0; rep < 6 && st == LQCD_OK; ++rep) {  // rep 0 warms up
-                    if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
-                    if (st == LQCD_OK)
-                        st = op_hop(c, out + fb, in, 1, prec, dag != 0, EPI_XPAY, red != 0, nullptr, in + fb, -0.1, 1,
-                                    fb, red ? SC_TMP + 7 : -1);
-                    if (st == LQCD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess)
-                        st = fail(LQCD_ERR_CUDA, "lqcd_tune: event");
-                    if (st == LQCD_OK && cudaEventSynchronize(e1) != cudaSuccess)
-                        st = fail(LQCD_ERR_CUDA, "lqcd_tune: sync");
-                    float t = 0.f;
-                    if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
-                }
+                time_launches(dag, red, ms);
                 // a smaller block has to be faster by 2 % to replace the larger one
                 if (st == LQCD_OK && ms < 0.98f * best) {
                     best = ms;
@@ -669,6 +677,20 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4])
             }
             c->tuned_block[prec][dag][red] = best_b;
             if (best_block) best_block[2 * dag + red] = best_b;
+            if (red) {
+                int best_s = 0;
+                for (int si = 1; si < 4 && st == LQCD_OK; ++si) {
+                    c->tuned_spt[prec][dag] = spts[si];
+                    float ms = 0.f;
+                    time_launches(dag, red, ms);
+                    if (st == LQCD_OK && ms < 0.98f * best) {
+                        best = ms;
+                        best_s = spts[si];
+                    }
+                }
+                c->tuned_spt[prec][dag] = best_s;
+                if (best_sites) best_sites[dag] = best_s;
+            }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -55,6 +55,7 @@ struct DslashArgs {
     int s_num, s_num2;       // alpha = (scal[s_num] + scal[s_num2]) / (scal[s_den] + scal[s_den2])
     int s_den, s_den2;
     const int* skip;         // per rhs: nonzero = converged, do nothing (may be nullptr)
+    int sites_per_thread;    // reducing launches: grid of Vh / (block * this); 0 = one wave of blocks
 };
 
 // ---- spin projection (1 + S g_mu), S = -1 or +1, onto two colour vectors
@@ -411,7 +412,14 @@ cudaError_t launch_dslash_t(const DslashArgs& A, int nrhs, int block, cudaStream
         wave[bi] = per_sm > 0 && sms > 0 ? per_sm * sms : 1 << 30;
     }
     int gx = (A.g.Vh + block - 1) / block;
-    if ((RED || EPI == EPI_CG) && gx > wave[bi]) gx = wave[bi];
+    if (RED || EPI == EPI_CG) {
+        if (A.sites_per_thread > 0) {
+            const long per_block = (long)block * A.sites_per_thread;
+            gx = (int)((A.g.Vh + per_block - 1) / per_block);
+        } else if (gx > wave[bi]) {
+            gx = wave[bi];
+        }
+    }
     dim3 grid(gx, nrhs);
     dslash_kernel<PG, PS, RECON, DAG, EPI, RED><<<grid, block, 0, s>>>(A);
     return cudaGetLastError();

@@ -105,6 +105,8 @@ struct lqcd_ctx {
     long launches;           // kernels launched by this context (all kinds)
     // tuned threads per block: [precision mode][dag][launch reduces into a scalar] (0 = default)
     int tuned_block[lqcd::NMODES][2][2];
+    // tuned sites per thread of the reducing launches: [precision mode][dag] (0 = one wave of blocks)
+    int tuned_spt[lqcd::NMODES][2];
 
     // bytes of one single-parity spinor field of precision mode m
     size_t field_bytes(int m) const { return lqcd::spinor_field_bytes(lqcd::mode_ps(m), g.stride); }

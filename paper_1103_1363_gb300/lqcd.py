@@ -90,7 +90,7 @@ _SIGS = {
     "lqcd_set_preconditioner_sap": [_P, _P, _I, _I],
     "lqcd_harmonic_ritz": [_I, _P, _I, _I, _P, _P],
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
-    "lqcd_tune": [_P, _I, C.POINTER(C.c_int)],
+    "lqcd_tune": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
@@ -307,11 +307,13 @@ def lqcd_sap_apply(ctx, z, r, block, ncycle=1, nmr=4):
 
 
 def lqcd_tune(ctx, prec):
-    """Autotune the hopping kernels' block size; returns the choices
-    (plain, plain reducing, dagger, dagger reducing)."""
+    """Autotune the hopping kernels; returns {"block": (plain, plain reducing,
+    dagger, dagger reducing), "sites_per_thread": (plain reducing, dagger
+    reducing)} (0 sites per thread: one wave of resident blocks)."""
     best = (C.c_int * 4)()
-    _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best), "lqcd_tune")
-    return tuple(best)
+    sites = (C.c_int * 2)()
+    _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best, sites), "lqcd_tune")
+    return {"block": tuple(best), "sites_per_thread": tuple(sites)}
 
 
 def lqcd_profile_enable(ctx, enable=True):

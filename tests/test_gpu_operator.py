@@ -201,6 +201,7 @@ def test_autotuner_keeps_results(lq):
     lat.gauge_load(U)
     for prec in ("f32", "f16"):
         best = lq.lqcd_tune(lat.ctx, prec)
-        assert all(b in (32, 64, 96, 128) for b in best)
+        assert all(b in (32, 64, 96, 128) for b in best["block"])
+        assert all(s in (0, 1, 4, 16) for s in best["sites_per_thread"])
         got = gpu_apply(lat, prec, psi, 1, 0, lambda o, i: lat.dslash(o, i, 0, prec=prec))
         assert rel(got, hop_ref(U, psi, dims, 0)) < TOL[prec]
