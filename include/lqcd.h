@@ -254,8 +254,12 @@ lqcd_status lqcd_dslash_schur_static(lqcd_ctx* ctx, void* out, const void* in, d
  * site order; the network's input and output are canonical FP32 spinors.
  * Weights: FP32 complex, layer after layer, each [9][4 C_out][4 C_in].
  * Gradients are dL/dRe W + i dL/dIm W.  bf16 = 1 runs the channel
- * contractions on the tensor cores with BF16 operands and FP32
- * accumulation; bf16 = 0 runs them in FP32. */
+ * contractions on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulators in tensor memory); bf16 = 0 runs them in FP32.  Inside the
+ * network activations are kept planar (per channel, six float4 planes over
+ * the sites); the calls below convert at the boundary, so callers always see
+ * the canonical layout.  A bounded device wait that expires inside a layer
+ * sets the error word (lqcd_sync returns LQCD_ERR_TIMEOUT). */
 typedef struct lqcd_net lqcd_net;
 /* channels[0..nlayers], channels[0] = channels[nlayers] = 1, each <= 12;
  * max_batch: largest batch of forward / training calls.  Needs F32 links. */
@@ -274,7 +278,8 @@ lqcd_status lqcd_net_get_weights(const lqcd_net* net, float* w, float* grad);
  * sum_h T_h^dag W_h^dag applied to `in`) on device activations. */
 lqcd_status lqcd_net_layer_apply(lqcd_net* net, int layer, int adjoint, float* out, const float* in, int batch);
 /* Weight gradient of one layer from its input activations and output
- * gradient, added into the net's gradient buffer (zeroed first if zero). */
+ * gradient, added into the net's gradient buffer (zeroed first if zero).
+ * Both layer calls take batch <= max_batch (LQCD_ERR_INVALID otherwise). */
 lqcd_status lqcd_net_layer_wgrad(lqcd_net* net, int layer, const float* in, const float* gout, int batch, int zero);
 /* out = N(in) for batch canonical FP32 spinors (device). */
 lqcd_status lqcd_net_forward(lqcd_net* net, float* out, const float* in, int batch);

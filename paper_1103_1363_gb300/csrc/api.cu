@@ -598,6 +598,7 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
     LQ_CUDA(cudaStreamSynchronize(c->stream));
     if (err & ERRW_CLOVER_SINGULAR) return fail(LQCD_ERR_CLOVER_SINGULAR, "singular clover block");
     if (err & ERRW_BREAKDOWN) return fail(LQCD_ERR_BREAKDOWN, "solver breakdown");
+    if (err & ERRW_TIMEOUT) return fail(LQCD_ERR_TIMEOUT, "a bounded device wait expired");
     return LQCD_OK;
     LQ_GUARD_END
 }

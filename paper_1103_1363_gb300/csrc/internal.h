@@ -30,7 +30,7 @@ lqcd_status cuda_fail(cudaError_t e, const char* where);
     } while (0)
 
 // device error word bits
-enum { ERRW_CLOVER_SINGULAR = 1, ERRW_BREAKDOWN = 2 };
+enum { ERRW_CLOVER_SINGULAR = 1, ERRW_BREAKDOWN = 2, ERRW_TIMEOUT = 4 };
 
 // Scalar slots per right-hand side (doubles).  The CG keeps rings of
 // |r|^2 and |M p|^2 values, one (even, odd) pair per iteration, so that

@@ -9,14 +9,22 @@
 // transport acts on colour, W on spin x channel, so the two commute; the
 // adjoint layer is therefore the same kernel with W'_h = W_{adj(h)}^dag.
 //
-// Activations: FP32 complex, [batch][site][channel][spin][colour], canonical
-// site order.  One CTA handles a tile of 64 consecutive sites: for each hop
-// it gathers the transported inputs of its 192 (site, colour) rows into
-// shared memory, then accumulates the real-ified product
+// Activations at the C ABI: FP32 complex, [batch][site][channel][spin][colour],
+// canonical site order.  Inside the network they are planar: per batch item
+// and channel, six float4 planes over the sites, plane q holding complex
+// components 2q and 2q+1 of the 12 values k = 3 spin + colour (a warp's
+// loads of consecutive sites are then one contiguous stretch).  Per hop, the transported inputs of a tile of sites are
+// gathered into shared memory, and the real-ified product
 //   OUT[row][n2] += X[row][k2] * B_h[k2][n2]
-// (k2 = 2*(ci*4+r) + {re, im}, n2 = 2*(co*4+s) + {re, im}) on the tensor
-// cores (BF16 operands, FP32 accumulation, mma.sync m16n8k16) or, for the
-// FP32 path, with FMAs.
+// (row = (site, colour), k2 = 2*(ci*4+r) + {re, im}, n2 = 2*(co*4+s) +
+// {re, im}) is accumulated over the nine hops:
+// - BF16 path: tcgen05 tensor cores.  A persistent CTA per SM takes tiles
+//   of 128 sites; the three colour rows of a site go to three M = 128 MMAs
+//   (K = 16 per instruction) whose FP32 accumulators live in tensor memory
+//   for all nine hops.  Operands are double-buffered in shared memory, so
+//   the gather of hop h+1 runs while the MMAs of hop h execute; one thread
+//   issues the MMAs and an mbarrier tracks their completion.
+// - FP32 path: FMAs on 64-site tiles, accumulators in registers.
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -27,6 +35,8 @@
 namespace lqcd {
 
 enum { NET_TS = 64, NET_ROWS = 3 * NET_TS, NET_THREADS = 256, NET_MAXC = 12, NET_PARTIALS = 64 };
+// tensor-core path: sites per tile (= MMA M), threads, minimum dynamic shared memory (one CTA per SM)
+enum { NTC_TS = 128, NTC_THREADS = 512, NTC_MIN_SMEM = 116 * 1024 };
 
 struct NetLayerArgs {
     int L[4];
@@ -37,37 +47,55 @@ struct NetLayerArgs {
     int cin, cout;
     int K2, N2;        // real-ified inner / outer sizes: 8 cin, 8 cout
     int K2p, N2p;      // padded to 16 / 8
-    const float* in;   // [batch][V][cin][4][3] complex
-    float* out;        // [batch][V][cout][4][3] complex
+    const float* in;   // planar activations, cin channels per batch item
+    float* out;        // planar activations, cout channels per batch item
     const float* Bf;   // FP32 real-ified weights [9][K2][N2]
-    const uint16_t* Bh;// BF16 real-ified weights [9][N2p][K2p] (n-major)
+    const uint16_t* Bh;// BF16 real-ified weights [9][N2p][K2p] in 8x8 core-matrix order (see prep)
+    int batch;         // tensor-core path: batch items (tiles are strided over batch x sites)
+    int tmem_cols;     // tensor-core path: allocated tensor-memory columns (power of 2 >= 3 N2p)
+    int* errw;         // device error word (bounded waits that expire set ERRW_TIMEOUT)
 };
 
 __host__ __device__ inline int adj_hop(int h) { return h == 0 ? 0 : (h % 2 == 1 ? h + 1 : h - 1); }
+
+// Planar layout of one batch item: float4 index of plane (channel ci, q) at site 0.
+__host__ __device__ inline size_t plane4(int V, int ci, int q) { return ((size_t)ci * 6 + q) * V; }
+
+// Complex value k = 3 spin + colour of channel ci at a site, as a float2 index.
+__device__ __forceinline__ size_t planar_c(int V, int ci, int k, int site)
+{
+    return (plane4(V, ci, k >> 1) + site) * 2 + (k & 1);
+}
 
 // Link for hop h at canonical site x: V (3x3 complex, 18 floats) and the
 // fermion sign; returns the neighbour site.
 template <int RECON>
 __device__ __forceinline__ int hop_link(const NetLayerArgs& a, int x, int h, float u[18], float& sign)
 {
-    int c[4];
+    const int L0 = a.L[0], L1 = a.L[1], L2 = a.L[2], L3 = a.L[3];
     int s = x;
-    c[0] = s % a.L[0]; s /= a.L[0];
-    c[1] = s % a.L[1]; s /= a.L[1];
-    c[2] = s % a.L[2];
-    c[3] = s / a.L[2];
+    const int c0 = s % L0;
+    s /= L0;
+    const int c1 = s % L1;
+    s /= L1;
+    const int c2 = s % L2;
+    const int c3 = s / L2;
     sign = 1.f;
     if (h == 0) return x;
     const int mu = (h - 1) / 2;
     const bool fwd = ((h - 1) % 2) == 0;
-    int n[4] = {c[0], c[1], c[2], c[3]};
-    n[mu] = fwd ? (c[mu] + 1 == a.L[mu] ? 0 : c[mu] + 1) : (c[mu] == 0 ? a.L[mu] - 1 : c[mu] - 1);
-    const int y = ((n[3] * a.L[2] + n[2]) * a.L[1] + n[1]) * a.L[0] + n[0];
-    if (a.tanti && mu == 3 && ((fwd && c[3] == a.L[3] - 1) || (!fwd && c[3] == 0))) sign = -1.f;
-    // forward: U_mu(x); backward: U_mu(y)^dag
+    int cm, Lm, st;  // coordinate, extent and site stride of direction mu
+    switch (mu) {
+    case 0: cm = c0; Lm = L0; st = 1; break;
+    case 1: cm = c1; Lm = L1; st = L0; break;
+    case 2: cm = c2; Lm = L2; st = L0 * L1; break;
+    default: cm = c3; Lm = L3; st = L0 * L1 * L2; break;
+    }
+    const int y = fwd ? (cm == Lm - 1 ? x - (Lm - 1) * st : x + st) : (cm == 0 ? x + (Lm - 1) * st : x - st);
+    if (a.tanti && mu == 3 && ((fwd && c3 == L3 - 1) || (!fwd && c3 == 0))) sign = -1.f;
+    // forward: U_mu(x); backward: U_mu(y)^dag, y of the other parity (all extents are even)
     const int site = fwd ? x : y;
-    const int* cc = fwd ? c : n;
-    const int par = (cc[0] + cc[1] + cc[2] + cc[3]) & 1;
+    const int par = (c0 + c1 + c2 + c3 + (fwd ? 0 : 1)) & 1;
     GaugeIO<P32, RECON>::load(a.gauge, a.stride, par, mu, site >> 1, u);
     if (!fwd) {
 #pragma unroll
@@ -89,13 +117,14 @@ __device__ __forceinline__ uint16_t f2bf(float f)
     return *reinterpret_cast<uint16_t*>(&b);
 }
 
-// Gather the transported inputs of hop h for the tile into shared memory:
-// X[row = site*3 + a][k2]; rows past V are zero.  The tile's links and
-// neighbours for the hop are staged once; then consecutive threads take
-// consecutive (channel, spin) pieces of the same neighbour, whose
-// activations are contiguous, so each warp reads one stretch of memory.
-template <int RECON, bool TC>
-__device__ __forceinline__ void gather_hop(const NetLayerArgs& a, const float* in_b, int tile0, int h, void* Xs,
+// Gather the transported inputs of hop h for a 64-site tile into shared
+// memory (FP32 path and weight gradient): X[row = site*3 + a][k2]; rows past
+// V are zero.  The tile's links and neighbours for the hop are staged once;
+// then consecutive threads take consecutive (channel, spin) pieces of the
+// same neighbour, whose activations are contiguous, so each warp reads one
+// stretch of memory.
+template <int RECON>
+__device__ __forceinline__ void gather_hop(const NetLayerArgs& a, const float* in_b, int tile0, int h, float* Xs,
                                            int xstride)
 {
     __shared__ float us[NET_TS][19];  // link (18 floats) and fermion sign per site of the tile
@@ -125,8 +154,10 @@ __device__ __forceinline__ void gather_hop(const NetLayerArgs& a, const float* i
         const int y = ys[sl];
         float o[6] = {0, 0, 0, 0, 0, 0};
         if (y >= 0 && k < nk) {
-            const float2* src = reinterpret_cast<const float2*>(in_b) + ((size_t)y * nk + k) * 3;
-            const float2 p0 = src[0], p1 = src[1], p2 = src[2];
+            const float2* src = reinterpret_cast<const float2*>(in_b);
+            const int ci = k >> 2, r = k & 3;  // k = ci * 4 + spin: colours 0..2 are k' = 3 r + a
+            const float2 p0 = src[planar_c(a.V, ci, 3 * r, y)], p1 = src[planar_c(a.V, ci, 3 * r + 1, y)],
+                         p2 = src[planar_c(a.V, ci, 3 * r + 2, y)];
             if (h == 0) {
                 o[0] = p0.x; o[1] = p0.y; o[2] = p1.x; o[3] = p1.y; o[4] = p2.x; o[5] = p2.y;
             } else {
@@ -142,27 +173,389 @@ __device__ __forceinline__ void gather_hop(const NetLayerArgs& a, const float* i
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const int row = sl * 3 + r;
-            if (TC) {
-                uint32_t v = (uint32_t)f2bf(o[2 * r]) | ((uint32_t)f2bf(o[2 * r + 1]) << 16);
-                reinterpret_cast<uint32_t*>(static_cast<uint16_t*>(Xs) + (size_t)row * xstride)[k] = v;
-            } else {
-                reinterpret_cast<float2*>(static_cast<float*>(Xs) + (size_t)row * xstride)[k] = make_float2(o[2 * r], o[2 * r + 1]);
-            }
+            reinterpret_cast<float2*>(Xs + (size_t)row * xstride)[k] = make_float2(o[2 * r], o[2 * r + 1]);
         }
     }
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2])
+// ---------------------------------------------------------------- tcgen05
+// Inline-PTX wrappers for the 5th-generation tensor cores (sm_100 family):
+// tensor-memory allocation, single-thread MMA issue with shared-memory
+// operand descriptors, completion through an mbarrier, and tensor-memory
+// loads for the epilogue.
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling.
+// The operand is tiled into core matrices of 8 rows x 16 bytes (128
+// contiguous bytes); lbo = bytes between core matrices adjacent in K, sbo =
+// bytes between adjacent 8-row groups.  Bits 46-47: descriptor version 1;
+// base offset, LBO mode and layout type (bits 49-52, 61-63) are 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Forward of one layer for every batch item (blockIdx.y) and tile (blockIdx.x).
-template <int RECON, bool TC>
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22 and M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Wait until the phase of parity `parity` has completed; false once
+// `limit_ns` of wall time have passed without that.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (now_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Warp-wide: allocate `ncols` tensor-memory columns (all 128 lanes); the
+// address is written to *slot.  Executed by one whole warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor cores' reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread; accumulate = 0
+// overwrites D.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// One arrival on *bar that also expects `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared (16-byte aligned, size a multiple of 16) that
+// completes `bytes` transactions on *bar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Arrive once on *bar when every MMA this thread issued so far has completed.
+__device__ __forceinline__ void commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 16 consecutive 32-bit columns of the warp's 32 lanes (lane quarter of the
+// warp within its warpgroup); completes with wait_ld.
+__device__ __forceinline__ void ld_x16(uint32_t taddr, uint32_t v[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+}  // namespace tc
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    return (uint32_t)f2bf(lo) | ((uint32_t)f2bf(hi) << 16);
+}
+
+// Neighbour of canonical site x (coordinates c0..c3) under hop h; h = 0 is x.
+__device__ __forceinline__ int hop_neighbour(const NetLayerArgs& a, int x, int c0, int c1, int c2, int c3, int h)
+{
+    if (h == 0) return x;
+    const int mu = (h - 1) / 2;
+    const bool fwd = ((h - 1) % 2) == 0;
+    int cm, Lm, st;
+    switch (mu) {
+    case 0: cm = c0; Lm = a.L[0]; st = 1; break;
+    case 1: cm = c1; Lm = a.L[1]; st = a.L[0]; break;
+    case 2: cm = c2; Lm = a.L[2]; st = a.L[0] * a.L[1]; break;
+    default: cm = c3; Lm = a.L[3]; st = a.L[0] * a.L[1] * a.L[2]; break;
+    }
+    return fwd ? (cm == Lm - 1 ? x - (Lm - 1) * st : x + st) : (cm == 0 ? x + (Lm - 1) * st : x - st);
+}
+
+// The 24 floats of channel ci at site y of planar activations (zeros for y < 0).
+__device__ __forceinline__ void load_channel(const float* in_b, int V, int ci, int y, float p[24])
+{
+    if (y >= 0) {
+        const float4* src = reinterpret_cast<const float4*>(in_b) + plane4(V, ci, 0) + y;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 v = __ldg(src + (size_t)q * V);
+            p[4 * q] = v.x; p[4 * q + 1] = v.y; p[4 * q + 2] = v.z; p[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 24; ++q) p[q] = 0.f;
+    }
+}
+
+// Upper bound of any wait on this kernel's own MMAs (a hop's MMAs take
+// microseconds); an expired wait sets ERRW_TIMEOUT and the CTA stops.
+#define NTC_WAIT_NS 2000000000ull
+
+// BF16 forward of one layer on the tensor cores.  Shared memory: two
+// operand stages, each X (3 colour blocks of 128 sites x K2p) and B_h
+// (N2p x K2p), both BF16 in core-matrix order; two link stages (per site:
+// the hop's link times the boundary sign, and the neighbour); then four
+// mbarriers (MMAs of stage s done, B_h of stage s landed) and the
+// tensor-memory address.  The first 128 threads stage hop h+1's links
+// while the others gather hop h (hop 0, the identity, needs none); slot 18
+// of a site's 19 floats is padding (odd stride: conflict-free reads).
+// Tensor memory: the accumulator of colour a in columns [a N2p, (a+1) N2p),
+// lane = site of the tile.  Thread (site sl = tid % 128, group tid / 128)
+// gathers channels group + 4 j; B_h arrives by one bulk copy per hop.
+template <int RECON>
+__global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetLayerArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    // thread group 0 stages links; groups 1.. gather and transport channels grp - 1 + TG j
+    constexpr int TG = NTC_THREADS / NTC_TS - 1, CPT = (NET_MAXC + TG - 1) / TG;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K2p = a.K2p, N2p = a.N2p;
+    const uint32_t blk = (uint32_t)NTC_TS * K2p * 2;  // one colour block of X
+    const uint32_t xbytes = 3 * blk, bbytes = (uint32_t)N2p * K2p * 2;
+    float* lbuf = reinterpret_cast<float*>(smem + 2 * xbytes + 2 * bbytes);              // [2][NTC_TS][19]
+    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(lbuf + 2 * NTC_TS * 19);              // [2]
+    uint64_t* b_bar = mma_bar + 2;                                                     // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 4);
+    const uint32_t sbo = (uint32_t)(K2p / 8) * 128;  // 8-row groups; K-adjacent core matrices are 128 B apart
+    const uint32_t idesc = tc::idesc_bf16_f32(NTC_TS, N2p);
+    const uint32_t ncols = (uint32_t)a.tmem_cols;
+
+    // zero both X stages once: the columns of channels >= cin (K padding) are never written
+    for (uint32_t e = tid; e < 2 * xbytes / 16; e += NTC_THREADS)
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) tc::mbar_init(&mma_bar[i], 1);
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int ntiles = (a.V + NTC_TS - 1) / NTC_TS;
+    const int total = ntiles * a.batch;
+    const int sl = tid & (NTC_TS - 1), grp = tid / NTC_TS;
+    uint32_t g = 0;       // hops whose MMAs were issued (each commits once to mma_bar[g & 1])
+    int copies = 0;       // bulk copies issued (hop g's lands on b_bar[g & 1])
+    bool failed = false;
+    // Each gathering thread walks the items (tile, hop h, channel c0 + TG j),
+    // j < nj, and loads one item ahead, so that a load is in flight while the
+    // previous item is transported (across the hop barrier and into the next tile).
+    const int cfirst = grp - 1;
+    const int nj = (grp > 0 && cfirst < a.cin) ? (a.cin - cfirst + TG - 1) / TG : 0;
+    float nxt[24];
+    if ((int)blockIdx.x < total && nj > 0) {
+        const int t = blockIdx.x, b = t / ntiles, x0 = (t - b * ntiles) * NTC_TS + sl;
+        load_channel(a.in + (size_t)b * a.V * a.cin * 24, a.V, cfirst, x0 < a.V ? x0 : -1, nxt);
+    }
+    bool wait_failed = false;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int b = t / ntiles, tile0 = (t - b * ntiles) * NTC_TS;
+        const float* in_b = a.in + (size_t)b * a.V * a.cin * 24;
+        const int x = tile0 + sl;
+        const int c0 = x % a.L[0], c1 = (x / a.L[0]) % a.L[1], c2 = (x / (a.L[0] * a.L[1])) % a.L[2],
+                  c3 = x / (a.L[0] * a.L[1] * a.L[2]);
+        const int tn = t + gridDim.x;  // this CTA's next tile
+        for (int h = 0; h < 9; ++h) {
+            const int s = g & 1;
+            unsigned char* const Xst = smem + s * xbytes;               // stage s: X
+            unsigned char* const Bst = smem + 2 * xbytes + s * bbytes;  // stage s: B_h
+            // stage s is free once the MMAs of hop g - 2 have completed (each
+            // thread waits for itself; a failure is shared at the barrier below)
+            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, NTC_WAIT_NS);
+            if (grp == 0 && h < 8) {  // links of hop h + 1 (read after this hop's barrier)
+                float un[18];
+                float sign = 1.f;
+                if (x < a.V) {
+                    hop_link<RECON>(a, x, h + 1, un, sign);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 18; ++k) un[k] = 0.f;
+                }
+                float* ls = lbuf + (((h + 1) & 1) * NTC_TS + sl) * 19;
+#pragma unroll
+                for (int k = 0; k < 18; ++k) ls[k] = sign * un[k];
+            }
+            if (tid == 0) {  // B_h, stored in core-matrix order: one contiguous bulk copy
+                tc::mbar_arrive_expect_tx(&b_bar[s], bbytes);
+                tc::bulk_g2s(Bst, a.Bh + (size_t)h * N2p * K2p, bbytes, &b_bar[s]);
+            }
+            ++copies;
+            float u[18];  // link of the hop times the boundary sign (staged at hop h - 1)
+            if (h > 0 && nj > 0) {
+                const float* ls = lbuf + ((h & 1) * NTC_TS + sl) * 19;
+#pragma unroll
+                for (int k = 0; k < 18; ++k) u[k] = ls[k];
+            }
+            const int yh = x < a.V ? hop_neighbour(a, x, c0, c1, c2, c3, h) : -1;
+            unsigned char* xrow = Xst + (sl >> 3) * sbo + (sl & 7) * 16;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                if (j >= nj) break;
+                const int ci = cfirst + TG * j;
+                float cur[24];
+#pragma unroll
+                for (int q = 0; q < 24; ++q) cur[q] = nxt[q];
+                if (j + 1 < nj) {
+                    load_channel(in_b, a.V, ci + TG, yh, nxt);
+                } else if (h < 8) {
+                    load_channel(in_b, a.V, cfirst, x < a.V ? hop_neighbour(a, x, c0, c1, c2, c3, h + 1) : -1, nxt);
+                } else if (tn < total) {
+                    const int bn = tn / ntiles, xn = (tn - bn * ntiles) * NTC_TS + sl;
+                    load_channel(a.in + (size_t)bn * a.V * a.cin * 24, a.V, cfirst, xn < a.V ? xn : -1, nxt);
+                }
+#pragma unroll
+                for (int ca = 0; ca < 3; ++ca) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        float re, im;
+                        if (h == 0) {
+                            re = cur[2 * (3 * r + ca)];
+                            im = cur[2 * (3 * r + ca) + 1];
+                        } else {
+                            re = 0.f;
+                            im = 0.f;
+#pragma unroll
+                            for (int cb = 0; cb < 3; ++cb) {
+                                const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                                const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
+                                re += ur * pr - ui * pi;
+                                im += ur * pi + ui * pr;
+                            }
+                        }
+                        w[r] = pack_bf16x2(re, im);
+                    }
+                    // k2 = 8 ci .. 8 ci + 7: one 16-byte row of core matrix (site group, ci)
+                    *reinterpret_cast<uint4*>(xrow + ca * blk + ci * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            tc::fence_proxy_async();
+            if (!wait_failed) wait_failed = !tc::mbar_wait(&b_bar[s], (g >> 1) & 1u, NTC_WAIT_NS);
+            if (__syncthreads_or(wait_failed)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t xa = tc::smem_addr(Xst), ba = tc::smem_addr(Bst);
+                for (int ca = 0; ca < 3; ++ca)
+                    for (int ks = 0; ks < K2p / 16; ++ks)
+                        tc::mma_bf16(tmem + ca * N2p, tc::smem_desc(xa + ca * blk + ks * 256, 128, sbo),
+                                     tc::smem_desc(ba + ks * 256, 128, sbo), idesc, (h > 0 || ks > 0) ? 1u : 0u);
+                tc::commit(&mma_bar[s]);
+            }
+            ++g;
+        }
+        if (failed) break;
+        {  // the tile's last MMAs (their commit covers every earlier one)
+            const uint32_t gl = g - 1;
+            const bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+        tc::fence_after();
+        // epilogue: warp w reads lanes 32 (w % 4) .. +31 (its sites); column
+        // chunks of 16 (8 complex outputs n = co * 4 + spin, i.e. two output
+        // channels) go round-robin to the four warpgroups; each channel's six
+        // float4 planes are written at the site, coalesced over the warp
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int site = tile0 + 32 * q4 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+        float4* out_b = reinterpret_cast<float4*>(a.out) + (size_t)b * a.V * a.cout * 6;
+        for (int c0 = 16 * wg; c0 < N2p; c0 += 16 * (NTC_THREADS / 128)) {
+            uint32_t v[3][16];
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) tc::ld_x16(trow + ca * N2p + c0, v[ca]);
+            tc::wait_ld();
+            if (site < a.V) {
+#pragma unroll
+                for (int hc = 0; hc < 2; ++hc) {
+                    const int co = c0 / 8 + hc;
+                    if (co >= a.cout) break;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        // complex k = 2q, 2q+1 of channel co: spin k / 3, colour k % 3
+                        const int k0 = 2 * q, k1 = 2 * q + 1;
+                        const int j0 = 4 * hc + k0 / 3, j1 = 4 * hc + k1 / 3;
+                        out_b[plane4(a.V, co, q) + site] =
+                            make_float4(__uint_as_float(v[k0 % 3][2 * j0]), __uint_as_float(v[k0 % 3][2 * j0 + 1]),
+                                        __uint_as_float(v[k1 % 3][2 * j1]), __uint_as_float(v[k1 % 3][2 * j1 + 1]));
+                    }
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();  // tensor memory read before the next tile's first MMA overwrites it
+    }
+    if (failed) {  // bounded waits for this CTA's own operations in flight, then free the tensor memory
+        if (copies > 0) {
+            const uint32_t gc = (uint32_t)copies - 1;
+            tc::mbar_wait(&b_bar[gc & 1], (gc >> 1) & 1u, NTC_WAIT_NS);
+        }
+        if (g > 0) {
+            const uint32_t gl = g - 1;
+            tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+        }
+        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// FP32 forward of one layer (64-site tiles, one CTA each, batch in blockIdx.y).
+template <int RECON>
 __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const NetLayerArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -171,112 +564,46 @@ __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const NetLayerAr
     const float* in_b = a.in + (size_t)b * a.V * a.cin * 24;
     float* out_b = a.out + (size_t)b * a.V * a.cout * 24;
     const int tid = threadIdx.x;
-    if (TC) {
-        // shared: X [192][K2p + 8] bf16, B [N2p][K2p + 8] bf16
-        const int xs = a.K2p + 8;
-        uint16_t* Xs = reinterpret_cast<uint16_t*>(smem);
-        uint16_t* Bs = Xs + NET_ROWS * xs;
-        const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-        const int NT = a.N2p / 8;                 // n tiles
-        const int mt0 = (warp % 4) * 3;           // 3 of the 12 m tiles
-        const int ntw = (NT + 1) / 2;             // n tiles per warp half
-        const int nt0 = (warp / 4) * ntw;
-        float acc[3][6][4];
+    // shared: X [192][K2 + 4] f32, B [K2][N2 + 4] f32; thread tile 6 rows x 12 cols
+    const int xs = a.K2p + 4, bs = a.N2p + 4;
+    float* Xs = reinterpret_cast<float*>(smem);
+    float* Bs = Xs + NET_ROWS * xs;
+    const int rb = tid / 8, cb = tid % 8;  // 32 row blocks x 8 column blocks
+    float acc[6][12];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 6; ++i)
 #pragma unroll
-            for (int j = 0; j < 6; ++j)
+        for (int j = 0; j < 12; ++j) acc[i][j] = 0.f;
+    for (int h = 0; h < 9; ++h) {
+        gather_hop<RECON>(a, in_b, tile0, h, Xs, xs);
+        const float* Bg = a.Bf + (size_t)h * a.K2 * a.N2;
+        for (int e = tid; e < a.K2 * a.N2; e += NET_THREADS) Bs[(e / a.N2) * bs + e % a.N2] = Bg[e];
+        __syncthreads();
+        for (int k = 0; k < a.K2; ++k) {
+            float xv[6], bv[12];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-        for (int h = 0; h < 9; ++h) {
-            gather_hop<RECON, true>(a, in_b, tile0, h, Xs, xs);
-            const uint16_t* Bg = a.Bh + (size_t)h * a.N2p * a.K2p;
-            for (int e = tid; e < a.N2p * a.K2p / 2; e += NET_THREADS) {
-                const int n = e / (a.K2p / 2), kk = e % (a.K2p / 2);
-                reinterpret_cast<uint32_t*>(Bs + (size_t)n * xs)[kk] = reinterpret_cast<const uint32_t*>(Bg)[e];
-            }
-            __syncthreads();
-            for (int k0 = 0; k0 < a.K2p; k0 += 16) {
-                uint32_t af[3][4];
+            for (int i = 0; i < 6; ++i) xv[i] = Xs[(rb * 6 + i) * xs + k];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int r0 = (mt0 + i) * 16 + gid;
-                    af[i][0] = *reinterpret_cast<const uint32_t*>(Xs + (size_t)r0 * xs + k0 + tig * 2);
-                    af[i][1] = *reinterpret_cast<const uint32_t*>(Xs + (size_t)(r0 + 8) * xs + k0 + tig * 2);
-                    af[i][2] = *reinterpret_cast<const uint32_t*>(Xs + (size_t)r0 * xs + k0 + 8 + tig * 2);
-                    af[i][3] = *reinterpret_cast<const uint32_t*>(Xs + (size_t)(r0 + 8) * xs + k0 + 8 + tig * 2);
-                }
+            for (int j = 0; j < 12; ++j) bv[j] = (cb * 12 + j < a.N2) ? Bs[k * bs + cb * 12 + j] : 0.f;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const int nt = nt0 + j;
-                    if (nt >= NT || j >= ntw) break;
-                    uint32_t bf[2];
-                    const int n = nt * 8 + gid;
-                    bf[0] = *reinterpret_cast<const uint32_t*>(Bs + (size_t)n * xs + k0 + tig * 2);
-                    bf[1] = *reinterpret_cast<const uint32_t*>(Bs + (size_t)n * xs + k0 + 8 + tig * 2);
+            for (int i = 0; i < 6; ++i)
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) mma_bf16_16816(acc[i][j], af[i], bf);
-                }
-            }
-            __syncthreads();
+                for (int j = 0; j < 12; ++j) acc[i][j] = fmaf(xv[i], bv[j], acc[i][j]);
         }
-        // epilogue: acc -> out[site][co][s][a] (complex)
+        __syncthreads();
+    }
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 6; ++i) {
+        const int row = rb * 6 + i;
+        const int site = tile0 + row / 3, col = row % 3;
+        if (site >= a.V) continue;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const int nt = nt0 + j;
-                if (nt >= NT || j >= ntw) break;
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int row = (mt0 + i) * 16 + gid + 8 * hh;
-                    const int n2 = nt * 8 + tig * 2;  // even: (re, im) of output n2/2
-                    const int site = tile0 + row / 3, col = row % 3, n = n2 / 2;
-                    if (site < a.V && n2 < a.N2)
-                        reinterpret_cast<float2*>(out_b)[((size_t)site * 4 * a.cout + n) * 3 + col] =
-                            make_float2(acc[i][j][2 * hh], acc[i][j][2 * hh + 1]);
-                }
-            }
-    } else {
-        // shared: X [192][K2 + 4] f32, B [K2][N2 + 4] f32; thread tile 6 rows x 12 cols
-        const int xs = a.K2p + 4, bs = a.N2p + 4;
-        float* Xs = reinterpret_cast<float*>(smem);
-        float* Bs = Xs + NET_ROWS * xs;
-        const int rb = tid / 8, cb = tid % 8;  // 32 row blocks x 8 column blocks
-        float acc[6][12];
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j < 12; ++j) acc[i][j] = 0.f;
-        for (int h = 0; h < 9; ++h) {
-            gather_hop<RECON, false>(a, in_b, tile0, h, Xs, xs);
-            const float* Bg = a.Bf + (size_t)h * a.K2 * a.N2;
-            for (int e = tid; e < a.K2 * a.N2; e += NET_THREADS) Bs[(e / a.N2) * bs + e % a.N2] = Bg[e];
-            __syncthreads();
-            for (int k = 0; k < a.K2; ++k) {
-                float xv[6], bv[12];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) xv[i] = Xs[(rb * 6 + i) * xs + k];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) bv[j] = (cb * 12 + j < a.N2) ? Bs[k * bs + cb * 12 + j] : 0.f;
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) acc[i][j] = fmaf(xv[i], bv[j], acc[i][j]);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const int row = rb * 6 + i;
-            const int site = tile0 + row / 3, col = row % 3;
-            if (site >= a.V) continue;
-#pragma unroll
-            for (int j = 0; j < 12; j += 2) {
-                const int n2 = cb * 12 + j;
-                if (n2 < a.N2)
-                    reinterpret_cast<float2*>(out_b)[((size_t)site * 4 * a.cout + n2 / 2) * 3 + col] =
-                        make_float2(acc[i][j], acc[i][j + 1]);
+        for (int j = 0; j < 12; j += 2) {
+            const int n2 = cb * 12 + j;
+            if (n2 < a.N2) {
+                const int n = n2 / 2;  // n = co * 4 + spin
+                reinterpret_cast<float2*>(out_b)[planar_c(a.V, n >> 2, 3 * (n & 3) + col, site)] =
+                    make_float2(acc[i][j], acc[i][j + 1]);
             }
         }
     }
@@ -303,13 +630,13 @@ __global__ void __launch_bounds__(NET_THREADS) net_wgrad_kernel(const NetLayerAr
     for (int q = 0; q < 9; ++q) accr[q] = acci[q] = 0.f;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int b = t / ntiles, tile0 = (t % ntiles) * NET_TS;
-        gather_hop<RECON, false>(a, a.in + (size_t)b * a.V * a.cin * 24, tile0, h, Xs, xs);
+        gather_hop<RECON>(a, a.in + (size_t)b * a.V * a.cin * 24, tile0, h, Xs, xs);
         const float* gb = gout + (size_t)b * a.V * a.cout * 24;
         for (int e = threadIdx.x; e < NET_ROWS * nn; e += NET_THREADS) {
             const int row = e / nn, n = e % nn;
             const int site = tile0 + row / 3, col = row % 3;
             float2 v = make_float2(0.f, 0.f);
-            if (site < a.V) v = reinterpret_cast<const float2*>(gb)[((size_t)site * nn + n) * 3 + col];
+            if (site < a.V) v = reinterpret_cast<const float2*>(gb)[planar_c(a.V, n >> 2, 3 * (n & 3) + col, site)];
             Gs[row * 2 * nn + 2 * n] = v.x;
             Gs[row * 2 * nn + 2 * n + 1] = v.y;
         }
@@ -343,8 +670,10 @@ __global__ void __launch_bounds__(NET_THREADS) net_wgrad_kernel(const NetLayerAr
 }
 
 // Real-ified weights from complex W[h][n][k]: FP32 B[h][k2][n2] and BF16
-// Bh[h][n2][k2] (zero padded).  With W' = adjoint-hop conjugate transpose
-// when `adjoint` (the layer's input gradient).
+// Bh[h] (N2p x K2p, zero padded), the latter in the tensor cores' K-major
+// core-matrix order: element (n2, k2) at (n2/8) (K2p/8) 64 + (k2/8) 64 +
+// (n2%8) 8 + k2%8.  With W' = adjoint-hop conjugate transpose when
+// `adjoint` (the layer's input gradient).
 __global__ void net_prep_weights_kernel(const float* W, int cin, int cout, int adjoint, float* Bf, uint16_t* Bh,
                                         int K2p, int N2p)
 {
@@ -374,7 +703,7 @@ __global__ void net_prep_weights_kernel(const float* W, int cin, int cout, int a
             else v = (k2 & 1) == 0 ? wi : wr;
             Bf[((size_t)h * K2 + k2) * N2 + n2] = v;
         }
-        Bh[e] = f2bf(v);
+        Bh[(size_t)h * N2p * K2p + (n2 / 8) * (K2p / 8) * 64 + (k2 / 8) * 64 + (n2 % 8) * 8 + k2 % 8] = f2bf(v);
     }
 }
 
@@ -389,9 +718,9 @@ __global__ void net_from_internal_kernel(Geom g, const char* in, size_t in_rb, f
     const size_t V = (size_t)2 * g.Vh;
     float v[24];
     SpinorIO<P32>::load(in + b * in_rb + par * spinor_field_bytes(P32, g.stride), g.stride, i, v);
-    float4* dst = reinterpret_cast<float4*>(act + ((size_t)b * V + full_index(g, c)) * 24);
+    float4* dst = reinterpret_cast<float4*>(act) + (size_t)b * V * 6 + full_index(g, c);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    for (int k = 0; k < 6; ++k) dst[(size_t)k * V] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
 __global__ void net_to_internal_kernel(Geom g, char* out, size_t out_rb, const float* act, int nb)
@@ -402,14 +731,29 @@ __global__ void net_to_internal_kernel(Geom g, char* out, size_t out_rb, const f
     int c[4];
     cb_coords(g, i, par, c);
     const size_t V = (size_t)2 * g.Vh;
-    const float4* src = reinterpret_cast<const float4*>(act + ((size_t)b * V + full_index(g, c)) * 24);
+    const float4* src = reinterpret_cast<const float4*>(act) + (size_t)b * V * 6 + full_index(g, c);
     float v[24];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        float4 q = src[k];
+        float4 q = src[(size_t)k * V];
         v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
     }
     SpinorIO<P32>::store(out + b * out_rb + par * spinor_field_bytes(P32, g.stride), g.stride, i, v);
+}
+
+// Canonical [b][site][ch][4][3] complex <-> planar activations of nb batch
+// items (to_planar = 1: canonical -> planar).  Thread e walks the planar
+// order, so the planar side is coalesced.
+__global__ void net_layout_kernel(const float4* src, float4* dst, int V, int ch, int nb, int to_planar)
+{
+    const size_t per = (size_t)V * ch * 6, total = per * nb;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / per, r = e - b * per;
+        const size_t site = r % V, cq = r / V;
+        const size_t can = b * per + (site * ch + cq / 6) * 6 + cq % 6;
+        if (to_planar) dst[e] = src[can];
+        else dst[can] = src[e];
+    }
 }
 
 // Loss L = (1/B) sum_b |y_b - e_b|^2 / |e_b|^2; gout_b = 2 (y_b - e_b) / (B |e_b|^2).
@@ -475,7 +819,7 @@ struct lqcd_net {
     uint16_t* Bh[8];
     float* BfA[8];         // adjoint (input-gradient) weights
     uint16_t* BhA[8];
-    float* act[9];         // activations per layer boundary: [max_batch][V][ch][4][3] complex
+    float* act[9];         // planar activations per layer boundary, max_batch items
     float* gact[2];        // gradient ping-pong buffers (max channels)
     double* red;           // loss reductions [max_batch][2]
     double* partials;      // loss reduction partials [max_batch][NET_PARTIALS][2]
@@ -490,7 +834,6 @@ namespace {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 int pad16(int x) { return (x + 15) / 16 * 16; }
-int pad8(int x) { return (x + 7) / 8 * 8; }
 
 NetLayerArgs layer_args(const lqcd_net* n, int l, bool adjoint, const float* in, float* out)
 {
@@ -507,34 +850,74 @@ NetLayerArgs layer_args(const lqcd_net* n, int l, bool adjoint, const float* in,
     a.K2 = 8 * a.cin;
     a.N2 = 8 * a.cout;
     a.K2p = pad16(a.K2);
-    a.N2p = pad8(a.N2);
+    a.N2p = pad16(a.N2);  // the M = 128 MMA takes N in multiples of 16
     a.in = in;
     a.out = out;
     a.Bf = adjoint ? n->BfA[l] : n->Bf[l];
     a.Bh = adjoint ? n->BhA[l] : n->Bh[l];
+    a.batch = 1;
+    int cols = 32;
+    while (cols < 3 * a.N2p) cols *= 2;
+    a.tmem_cols = cols;
+    a.errw = c->errw;
     return a;
 }
 
-size_t layer_smem(const NetLayerArgs& a, bool tc)
+// Dynamic shared memory of the tensor-core kernel: two stages of X, B_h and
+// links, four mbarriers and the tensor-memory address; at least NTC_MIN_SMEM, so
+// that one CTA runs per SM and its tensor-memory allocation never waits.
+size_t layer_smem_tc(const NetLayerArgs& a)
 {
-    if (tc) return (size_t)(NET_ROWS + a.N2p) * (a.K2p + 8) * 2;
+    const size_t need = 2 * ((size_t)3 * NTC_TS * a.K2p * 2 + (size_t)a.N2p * a.K2p * 2) + 2 * NTC_TS * 19 * 4 + 4 * 8 + 16;
+    return need > (size_t)NTC_MIN_SMEM ? need : (size_t)NTC_MIN_SMEM;
+}
+
+size_t layer_smem_f32(const NetLayerArgs& a)
+{
     return (size_t)NET_ROWS * (a.K2p + 4) * 4 + (size_t)a.K2 * (a.N2p + 4) * 4;
 }
 
-lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a, int batch)
+int sm_count()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 0;
+    }
+    return sms;
+}
+
+lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch)
 {
     lqcd_ctx* c = n->ctx;
-    const bool tc = n->bf16 != 0;
-    const size_t sm = layer_smem(a, tc);
-    dim3 grid((a.V + NET_TS - 1) / NET_TS, batch);
-#define LQ_NL(RC, TCV)                                                                                   \
-    do {                                                                                                 \
-        LQ_CUDA(cudaFuncSetAttribute(net_layer_kernel<RC, TCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-        net_layer_kernel<RC, TCV><<<grid, NET_THREADS, sm, c->stream>>>(a);                            \
-    } while (0)
-    if (c->cfg.recon == 12) { if (tc) LQ_NL(12, true); else LQ_NL(12, false); }
-    else { if (tc) LQ_NL(18, true); else LQ_NL(18, false); }
-#undef LQ_NL
+    NetLayerArgs a = a0;
+    a.batch = batch;
+    if (n->bf16) {
+        // persistent: one CTA per SM strides over the batch x site tiles
+        const int sms = sm_count();
+        if (sms <= 0) return fail(LQCD_ERR_CUDA, "net layer: no SM count");
+        const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
+        const size_t sm = layer_smem_tc(a);
+        const int grid = total < sms ? total : sms;
+        if (c->cfg.recon == 12) {
+            LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_layer_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(a);
+        } else {
+            LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_layer_tc_kernel<18><<<grid, NTC_THREADS, sm, c->stream>>>(a);
+        }
+    } else {
+        const size_t sm = layer_smem_f32(a);
+        dim3 grid((a.V + NET_TS - 1) / NET_TS, batch);
+        if (c->cfg.recon == 12) {
+            LQ_CUDA(cudaFuncSetAttribute(net_layer_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_layer_kernel<12><<<grid, NET_THREADS, sm, c->stream>>>(a);
+        } else {
+            LQ_CUDA(cudaFuncSetAttribute(net_layer_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_layer_kernel<18><<<grid, NET_THREADS, sm, c->stream>>>(a);
+        }
+    }
     LQ_CUDA(cudaGetLastError());
     c->launches++;
     return LQCD_OK;
@@ -556,6 +939,43 @@ lqcd_status prep_weights(lqcd_net* n)
 }
 
 size_t act_floats(const lqcd_net* n, int chn) { return (size_t)2 * n->ctx->g.Vh * chn * 24; }
+
+// Canonical <-> planar copy of `batch` activations with `ch` channels.
+lqcd_status convert_layout(lqcd_net* n, const float* src, float* dst, int ch, int batch, bool to_planar)
+{
+    lqcd_ctx* c = n->ctx;
+    const int V = 2 * c->g.Vh;
+    const size_t total = (size_t)V * ch * 6 * batch;
+    const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    net_layout_kernel<<<grid, 256, 0, c->stream>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst),
+                                                   V, ch, batch, to_planar ? 1 : 0);
+    LQ_CUDA(cudaGetLastError());
+    c->launches++;
+    return LQCD_OK;
+}
+
+// Weight gradient of one layer on planar activations (zeroing it first when `zero`).
+lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout, int batch, int zero)
+{
+    lqcd_ctx* c = n->ctx;
+    float* gl = n->gW + n->woff[layer];
+    const size_t nw = n->woff[layer + 1] - n->woff[layer];
+    if (zero) LQ_CUDA(cudaMemsetAsync(gl, 0, nw * 4, c->stream));
+    NetLayerArgs a = layer_args(n, layer, false, in, nullptr);
+    const size_t sm = (size_t)NET_ROWS * (a.K2p + 4) * 4 + (size_t)NET_ROWS * 8 * a.cout * 4;
+    const int ntiles = (a.V + NET_TS - 1) / NET_TS * batch;
+    dim3 grid(ntiles < 2 * 152 ? ntiles : 2 * 152, 9);
+    if (c->cfg.recon == 12) {
+        LQ_CUDA(cudaFuncSetAttribute(net_wgrad_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        net_wgrad_kernel<12><<<grid, NET_THREADS, sm, c->stream>>>(a, gout, batch, gl);
+    } else {
+        LQ_CUDA(cudaFuncSetAttribute(net_wgrad_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        net_wgrad_kernel<18><<<grid, NET_THREADS, sm, c->stream>>>(a, gout, batch, gl);
+    }
+    LQ_CUDA(cudaGetLastError());
+    c->launches++;
+    return LQCD_OK;
+}
 
 }  // namespace
 
@@ -616,8 +1036,8 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
         size_t oW = take(w * 4), ogW = take(w * 4), om1 = take(w * 4), om2 = take(w * 4);
         size_t oB[8], oBh[8], oBA[8], oBhA[8];
         for (int l = 0; l < nlayers; ++l) {
-            const int K2p = pad16(8 * channels[l]), N2p = pad8(8 * channels[l + 1]);
-            const int K2pa = pad16(8 * channels[l + 1]), N2pa = pad8(8 * channels[l]);
+            const int K2p = pad16(8 * channels[l]), N2p = pad16(8 * channels[l + 1]);
+            const int K2pa = pad16(8 * channels[l + 1]), N2pa = pad16(8 * channels[l]);
             oB[l] = take((size_t)9 * K2p * N2p * 4);
             oBh[l] = take((size_t)9 * K2p * N2p * 2);
             oBA[l] = take((size_t)9 * K2pa * N2pa * 4);
@@ -727,8 +1147,12 @@ lqcd_status lqcd_net_get_weights(const lqcd_net* n, float* w, float* grad)
 lqcd_status lqcd_net_layer_apply(lqcd_net* n, int layer, int adjoint, float* out, const float* in, int batch)
 {
     if (!n || !n->ws || !out || !in) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_apply: bad argument");
-    if (layer < 0 || layer >= n->nlayers || batch < 1) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_apply: bad layer/batch");
-    return run_layer(n, layer_args(n, layer, adjoint != 0, in, out), batch);
+    if (layer < 0 || layer >= n->nlayers || batch < 1 || batch > n->max_batch)
+        return fail(LQCD_ERR_INVALID, "lqcd_net_layer_apply: bad layer/batch");
+    const NetLayerArgs a = layer_args(n, layer, adjoint != 0, n->gact[0], n->gact[1]);
+    LQ_TRY(convert_layout(n, in, n->gact[0], a.cin, batch, true));
+    LQ_TRY(run_layer(n, a, batch));
+    return convert_layout(n, n->gact[1], out, a.cout, batch, false);
 }
 
 // Weight gradient of one layer (accumulated into the net's gradient buffer
@@ -736,25 +1160,11 @@ lqcd_status lqcd_net_layer_apply(lqcd_net* n, int layer, int adjoint, float* out
 lqcd_status lqcd_net_layer_wgrad(lqcd_net* n, int layer, const float* in, const float* gout, int batch, int zero)
 {
     if (!n || !n->ws || !in || !gout) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_wgrad: bad argument");
-    if (layer < 0 || layer >= n->nlayers || batch < 1) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_wgrad: bad layer");
-    lqcd_ctx* c = n->ctx;
-    float* gl = n->gW + n->woff[layer];
-    const size_t nw = n->woff[layer + 1] - n->woff[layer];
-    if (zero) LQ_CUDA(cudaMemsetAsync(gl, 0, nw * 4, c->stream));
-    NetLayerArgs a = layer_args(n, layer, false, in, nullptr);
-    const size_t sm = (size_t)NET_ROWS * (a.K2p + 4) * 4 + (size_t)NET_ROWS * 8 * a.cout * 4;
-    const int ntiles = (a.V + NET_TS - 1) / NET_TS * batch;
-    dim3 grid(ntiles < 2 * 152 ? ntiles : 2 * 152, 9);
-    if (c->cfg.recon == 12) {
-        LQ_CUDA(cudaFuncSetAttribute(net_wgrad_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        net_wgrad_kernel<12><<<grid, NET_THREADS, sm, c->stream>>>(a, gout, batch, gl);
-    } else {
-        LQ_CUDA(cudaFuncSetAttribute(net_wgrad_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        net_wgrad_kernel<18><<<grid, NET_THREADS, sm, c->stream>>>(a, gout, batch, gl);
-    }
-    LQ_CUDA(cudaGetLastError());
-    c->launches++;
-    return LQCD_OK;
+    if (layer < 0 || layer >= n->nlayers || batch < 1 || batch > n->max_batch)
+        return fail(LQCD_ERR_INVALID, "lqcd_net_layer_wgrad: bad layer/batch");
+    LQ_TRY(convert_layout(n, in, n->gact[0], n->ch[layer], batch, true));
+    LQ_TRY(convert_layout(n, gout, n->gact[1], n->ch[layer + 1], batch, true));
+    return run_wgrad(n, layer, n->gact[0], n->gact[1], batch, zero);
 }
 
 // Whole-net forward on canonical FP32 complex spinors (batch items):
@@ -763,12 +1173,9 @@ lqcd_status lqcd_net_forward(lqcd_net* n, float* out, const float* in, int batch
 {
     if (!n || !n->ws || !out || !in) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: bad argument");
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: batch out of range");
-    lqcd_ctx* c = n->ctx;
-    const size_t bytes = (size_t)batch * act_floats(n, 1) * 4;
-    LQ_CUDA(cudaMemcpyAsync(n->act[0], in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    LQ_TRY(convert_layout(n, in, n->act[0], 1, batch, true));
     LQ_TRY(net_forward_all(n, batch));
-    LQ_CUDA(cudaMemcpyAsync(out, n->act[n->nlayers], bytes, cudaMemcpyDeviceToDevice, c->stream));
-    return LQCD_OK;
+    return convert_layout(n, n->act[n->nlayers], out, 1, batch, false);
 }
 
 // One training step on `batch` pairs (r, e) of canonical FP32 complex
@@ -782,21 +1189,23 @@ lqcd_status lqcd_net_train_step(lqcd_net* n, const float* r, const float* e, int
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_train_step: batch out of range");
     lqcd_ctx* c = n->ctx;
     const size_t n_per = act_floats(n, 1);
-    LQ_CUDA(cudaMemcpyAsync(n->act[0], r, (size_t)batch * n_per * 4, cudaMemcpyDeviceToDevice, c->stream));
+    LQ_TRY(convert_layout(n, r, n->act[0], 1, batch, true));
+    LQ_TRY(convert_layout(n, e, n->gact[1], 1, batch, true));  // planar target; gact[1] is free until the backward
     LQ_TRY(net_forward_all(n, batch));
+    const float* ep = n->gact[1];
     // loss and its gradient
     const int nb = 256;
     dim3 g1(NET_PARTIALS, batch);
-    net_loss_reduce_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], e, n_per, n->partials, 2 * NET_PARTIALS,
+    net_loss_reduce_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], ep, n_per, n->partials, 2 * NET_PARTIALS,
                                                      n->tickets, n->red);
     LQ_CUDA(cudaGetLastError());
-    net_loss_grad_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], e, n_per, n->red, batch, n->gact[0]);
+    net_loss_grad_kernel<<<g1, nb, 0, c->stream>>>(n->act[n->nlayers], ep, n_per, n->red, batch, n->gact[0]);
     LQ_CUDA(cudaGetLastError());
     c->launches += 2;
     // backward
     int cur = 0;
     for (int l = n->nlayers - 1; l >= 0; --l) {
-        LQ_TRY(lqcd_net_layer_wgrad(n, l, n->act[l], n->gact[cur], batch, 1));
+        LQ_TRY(run_wgrad(n, l, n->act[l], n->gact[cur], batch, 1));
         if (l > 0) {
             LQ_TRY(run_layer(n, layer_args(n, l, true, n->gact[cur], n->gact[1 - cur]), batch));
             cur = 1 - cur;

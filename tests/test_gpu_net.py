@@ -39,27 +39,33 @@ def lq():
     return require_cuda()
 
 
-def make(lq, channels, bf16, U, max_batch=2):
-    lat = lq.Lattice(DIMS, max_nrhs=1)
+def make(lq, channels, bf16, U, max_batch=2, dims=DIMS):
+    lat = lq.Lattice(dims, max_nrhs=1)
     lat.gauge_load(U)
     net = lq.Net(lat, channels, bf16=bf16, max_batch=max_batch)
     return lat, net
 
 
-@pytest.mark.parametrize("bf16", [False, True])
-def test_layers_forward_adjoint_wgrad(lq, bf16):
-    U = synth.smooth_gauge(DIMS, 0.5, 31)
+# 4x4x6x8: 768 sites, six full 128-site tiles of the tensor-core kernel;
+# 4x4x6x6: 576 sites, a ragged last tile (64 sites); 2x2x2x2: one tile
+# that is mostly padding; odd widths exercise the K and N padding.
+CASES = [(DIMS, (1, 12, 12, 1), False), (DIMS, (1, 12, 12, 1), True), ((4, 4, 6, 6), (1, 12, 12, 1), True),
+         ((2, 2, 2, 2), (1, 5, 3, 1), True)]
+
+
+@pytest.mark.parametrize("dims,chans,bf16", CASES, ids=["f32", "bf16", "bf16-ragged", "bf16-tiny-odd"])
+def test_layers_forward_adjoint_wgrad(lq, dims, chans, bf16):
+    U = synth.smooth_gauge(dims, 0.5, 31)
     rng = np.random.default_rng(0)
-    chans = (1, 12, 12, 1)
     Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
-    lat, net = make(lq, chans, bf16, U)
+    lat, net = make(lq, chans, bf16, U, dims=dims)
     net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
     tol = 2e-2 if bf16 else 1e-5
     B = 2
     for l in range(3):
         cin, cout = chans[l], chans[l + 1]
-        x = field(DIMS, cin, 40 + l, B)
-        g = field(DIMS, cout, 50 + l, B)
+        x = field(dims, cin, 40 + l, B)
+        g = field(dims, cout, 50 + l, B)
         out = torch.empty(x.shape[:5] + (cout, 4, 3), dtype=torch.complex64, device="cuda")
         net.layer_apply(l, out, dev(x), batch=B)
         gin = torch.empty(x.shape, dtype=torch.complex64, device="cuda")
