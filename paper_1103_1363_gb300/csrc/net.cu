@@ -554,6 +554,197 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// BF16 weight gradient of one layer on the tensor cores.  For hop h =
+// blockIdx.y, D[k2][n2] = sum over the (site, colour) rows of X[row][k2]
+// G[row][n2], with X the transported inputs and G the output gradient, both
+// real-ified BF16 tiles in the forward kernel's layout (rows = sites,
+// 16-byte rows of 8 consecutive k2 or n2 values) and read here as MN-major
+// operands: M = k2 padded to 128, N = n2 padded to 16, K = the 128 sites of
+// a colour block.  All tiles of the CTA accumulate into the same FP32
+// tensor memory.  The epilogue forms the complex gradient
+//   G_h[n][k] += (D[2k][2n] + D[2k+1][2n+1]) + i (D[2k][2n+1] - D[2k+1][2n])
+// (lanes 2k and 2k+1 exchange values by shuffles) and adds it with atomics.
+// Thread (site sl, group grp) loads the input channels grp + 4 j and the
+// output-gradient channels grp + 4 j, one item ahead; group 0 also stages the
+// links of the CTA's next tile.
+template <int RECON>
+__global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_tc_kernel(const NetLayerArgs a, const float* gout, float* gW)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int G4 = NTC_THREADS / NTC_TS, CPT = (NET_MAXC + G4 - 1) / G4;
+    constexpr int MX = 128;  // k2 padded to the MMA's M
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int h = blockIdx.y;
+    const int N2p = a.N2p;
+    const int nk = 4 * a.cin, nn = 4 * a.cout;
+    const uint32_t sbox = (MX / 8) * 128, sbog = (uint32_t)(N2p / 8) * 128;  // bytes between 8-site groups
+    const uint32_t blkx = (uint32_t)NTC_TS * MX * 2, blkg = (uint32_t)NTC_TS * N2p * 2;
+    unsigned char* const Xs = smem;
+    unsigned char* const Gs = smem + 3 * blkx;
+    float* lbuf = reinterpret_cast<float*>(Gs + 3 * blkg);  // [2][NTC_TS][19]
+    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(lbuf + 2 * NTC_TS * 19);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 1);
+    const uint32_t idesc = tc::idesc_bf16_f32(MX, N2p) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const uint32_t ncols = (uint32_t)a.tmem_cols;
+
+    for (uint32_t e = tid; e < 3 * (blkx + blkg) / 16; e += NTC_THREADS)  // K and N padding stays zero
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) tc::mbar_init(mma_bar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+
+    const int ntiles = (a.V + NTC_TS - 1) / NTC_TS;
+    const int total = ntiles * a.batch;
+    const int sl = tid & (NTC_TS - 1), grp = tid / NTC_TS;
+    const int nX = grp < a.cin ? (a.cin - grp + G4 - 1) / G4 : 0;
+    const int nG = grp < a.cout ? (a.cout - grp + G4 - 1) / G4 : 0;
+    const int nI = nX + nG;
+    // links of hop h (times the boundary sign) for the sites of tile t
+    auto stage_links = [&](int t, int slot) {
+        const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
+        float un[18];
+        float sign = 1.f;
+        if (x < a.V) {
+            hop_link<RECON>(a, x, h, un, sign);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) un[q] = 0.f;
+        }
+        float* ls = lbuf + (slot * NTC_TS + sl) * 19;
+#pragma unroll
+        for (int q = 0; q < 18; ++q) ls[q] = sign * un[q];
+    };
+    // item i of tile t: input channel grp + 4 i at the hop's neighbour, then
+    // output-gradient channel grp + 4 (i - nX) at the site
+    auto load_item = [&](int t, int i, float p[24]) {
+        const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
+        if (i < nX) {
+            int y = -1;
+            if (x < a.V) {
+                const int c0 = x % a.L[0], c1 = (x / a.L[0]) % a.L[1], c2 = (x / (a.L[0] * a.L[1])) % a.L[2],
+                          c3 = x / (a.L[0] * a.L[1] * a.L[2]);
+                y = hop_neighbour(a, x, c0, c1, c2, c3, h);
+            }
+            load_channel(a.in + (size_t)b * a.V * a.cin * 24, a.V, grp + G4 * i, y, p);
+        } else {
+            load_channel(gout + (size_t)b * a.V * a.cout * 24, a.V, grp + G4 * (i - nX), x < a.V ? x : -1, p);
+        }
+    };
+    float nxt[24];
+    if ((int)blockIdx.x < total) {
+        if (grp == 0 && h > 0) stage_links(blockIdx.x, 0);
+        if (nI > 0) load_item(blockIdx.x, 0, nxt);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    int k = 0;  // tiles of this CTA so far (tile k commits once to mma_bar)
+    bool wait_failed = false, failed = false;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int tn = t + gridDim.x;
+        // the operand tiles are free once the MMAs of tile k - 1 have completed
+        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (grp == 0 && h > 0 && tn < total) stage_links(tn, (k + 1) & 1);
+        float u[18];
+        if (h > 0 && nX > 0) {
+            const float* ls = lbuf + ((k & 1) * NTC_TS + sl) * 19;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) u[q] = ls[q];
+        }
+        const uint32_t rowoff = (sl & 7) * 16;  // row of the site within its 8-site core matrix
+#pragma unroll
+        for (int i = 0; i < 2 * CPT; ++i) {
+            if (i >= nI) break;
+            float cur[24];
+#pragma unroll
+            for (int q = 0; q < 24; ++q) cur[q] = nxt[q];
+            if (i + 1 < nI) load_item(t, i + 1, nxt);
+            else if (tn < total) load_item(tn, 0, nxt);
+            const bool isx = i < nX;
+            const int ch = grp + G4 * (isx ? i : i - nX);
+            unsigned char* dst = isx ? Xs + (sl >> 3) * sbox + ch * 128 + rowoff
+                                     : Gs + (sl >> 3) * sbog + ch * 128 + rowoff;
+            const uint32_t blk = isx ? blkx : blkg;
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) {
+                uint32_t w[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float re, im;
+                    if (!isx || h == 0) {
+                        re = cur[2 * (3 * r + ca)];
+                        im = cur[2 * (3 * r + ca) + 1];
+                    } else {
+                        re = 0.f;
+                        im = 0.f;
+#pragma unroll
+                        for (int cb = 0; cb < 3; ++cb) {
+                            const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                            const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
+                            re += ur * pr - ui * pi;
+                            im += ur * pi + ui * pr;
+                        }
+                    }
+                    w[r] = pack_bf16x2(re, im);
+                }
+                *reinterpret_cast<uint4*>(dst + ca * blk) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tc::fence_proxy_async();
+        if (__syncthreads_or(wait_failed)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t xa = tc::smem_addr(Xs), ga = tc::smem_addr(Gs);
+            for (int ca = 0; ca < 3; ++ca)
+                for (int ks = 0; ks < NTC_TS / 16; ++ks)
+                    tc::mma_bf16(tmem, tc::smem_desc(xa + ca * blkx + ks * 2 * sbox, sbox, 128),
+                                 tc::smem_desc(ga + ca * blkg + ks * 2 * sbog, sbog, 128), idesc,
+                                 (k > 0 || ca > 0 || ks > 0) ? 1u : 0u);
+            tc::commit(mma_bar);
+        }
+    }
+    if (!failed && k > 0) {
+        const bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (__syncthreads_or(!ok)) failed = true;
+    }
+    if (!failed && k > 0) {
+        tc::fence_after();
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int k2 = 32 * q4 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+        for (int c0 = 16 * wg; c0 < N2p; c0 += 16 * (NTC_THREADS / 128)) {
+            uint32_t v[16];
+            tc::ld_x16(trow + c0, v);
+            tc::wait_ld();
+            float pv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pv[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
+            const int kk = k2 >> 1;
+            if ((k2 & 1) == 0 && kk < nk) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int n = c0 / 2 + i;
+                    if (n >= nn) break;
+                    float* dst = gW + (((size_t)h * nn + n) * nk + kk) * 2;
+                    atomicAdd(dst, __uint_as_float(v[2 * i]) + pv[2 * i + 1]);
+                    atomicAdd(dst + 1, __uint_as_float(v[2 * i + 1]) - pv[2 * i]);
+                }
+            }
+        }
+    }
+    if (failed) {  // bounded wait for this CTA's MMAs in flight, then free the tensor memory
+        if (k > 0) tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
 // FP32 forward of one layer (64-site tiles, one CTA each, batch in blockIdx.y).
 template <int RECON>
 __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const NetLayerArgs a)
@@ -962,6 +1153,31 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
     const size_t nw = n->woff[layer + 1] - n->woff[layer];
     if (zero) LQ_CUDA(cudaMemsetAsync(gl, 0, nw * 4, c->stream));
     NetLayerArgs a = layer_args(n, layer, false, in, nullptr);
+    if (n->bf16) {
+        // tensor cores: one CTA per SM, sms / 9 CTAs per hop, each over a stride of the batch x site tiles
+        const int sms = sm_count();
+        if (sms <= 0) return fail(LQCD_ERR_CUDA, "net wgrad: no SM count");
+        a.batch = batch;
+        int cols = 32;
+        while (cols < a.N2p) cols *= 2;
+        a.tmem_cols = cols;
+        const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
+        int per_hop = sms / 9 > 0 ? sms / 9 : 1;
+        if (per_hop > total) per_hop = total;
+        size_t sm = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 2 * NTC_TS * 19 * 4 + 16;
+        if (sm < (size_t)NTC_MIN_SMEM) sm = NTC_MIN_SMEM;
+        dim3 grid(per_hop, 9);
+        if (c->cfg.recon == 12) {
+            LQ_CUDA(cudaFuncSetAttribute(net_wgrad_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_wgrad_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(a, gout, gl);
+        } else {
+            LQ_CUDA(cudaFuncSetAttribute(net_wgrad_tc_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            net_wgrad_tc_kernel<18><<<grid, NTC_THREADS, sm, c->stream>>>(a, gout, gl);
+        }
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+        return LQCD_OK;
+    }
     const size_t sm = (size_t)NET_ROWS * (a.K2p + 4) * 4 + (size_t)NET_ROWS * 8 * a.cout * 4;
     const int ntiles = (a.V + NET_TS - 1) / NET_TS * batch;
     dim3 grid(ntiles < 2 * 152 ? ntiles : 2 * 152, 9);

@@ -3,8 +3,9 @@ oracle: each layer, its adjoint (input gradient) and its weight gradient;
 the whole-network gradient of a training step against oracle backprop.
 
 Tolerances: FP32 path rel-L2 <= 1e-5 (FP32 rounding of sums of ~900
-terms); BF16 tensor-core path <= 2e-2 (8-bit mantissa operands, FP32
-accumulation) and its error is printed."""
+terms); BF16 tensor-core path (forward, adjoint and weight gradient)
+<= 2e-2 (8-bit mantissa operands, FP32 accumulation) and its error is
+printed."""
 import numpy as np
 import pytest
 import torch
@@ -81,15 +82,16 @@ def test_layers_forward_adjoint_wgrad(lq, dims, chans, bf16):
         e1, e2 = rel(out.cpu().numpy(), want_out), rel(gin.cpu().numpy(), want_gin)
         e3 = rel(gW, want_gW)
         print("layer %d bf16=%d: fwd %.2e adj %.2e wgrad %.2e" % (l, bf16, e1, e2, e3))
-        assert e1 < tol and e2 < tol and e3 < 1e-5
+        assert e1 < tol and e2 < tol and e3 < tol
 
 
-def test_train_step_gradient_matches_oracle_backprop(lq):
+@pytest.mark.parametrize("bf16", [False, True])
+def test_train_step_gradient_matches_oracle_backprop(lq, bf16):
     U = synth.smooth_gauge(DIMS, 0.5, 32)
     rng = np.random.default_rng(1)
     chans = (1, 4, 3, 1)
     Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
-    lat, net = make(lq, chans, False, U, max_batch=2)
+    lat, net = make(lq, chans, bf16, U, max_batch=2)
     net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
     B = 2
     r = field(DIMS, 1, 60, B)
@@ -106,7 +108,7 @@ def test_train_step_gradient_matches_oracle_backprop(lq):
     y = acts[-1]
     en2 = np.array([np.sum(np.abs(e[b]) ** 2) for b in range(B)])
     want_loss = np.mean([np.sum(np.abs(y[b] - e[b]) ** 2) / en2[b] for b in range(B)])
-    assert abs(loss - want_loss) / want_loss < 1e-5
+    assert abs(loss - want_loss) / want_loss < (2e-2 if bf16 else 1e-5)
     g = np.stack([2 * (y[b] - e[b]) / (B * en2[b]) for b in range(B)])
     want = []
     for l in range(2, -1, -1):
@@ -114,8 +116,8 @@ def test_train_step_gradient_matches_oracle_backprop(lq):
         g = np.stack([oracle.net_layer_adj(U, Ws[l], g[b]) for b in range(B)])
     want = np.concatenate([w.reshape(-1) for w in want])
     err = rel(grad.numpy(), want)
-    print("train-step gradient rel err %.2e" % err)
-    assert err < 1e-5
+    print("train-step gradient rel err %.2e (bf16=%d)" % (err, bf16))
+    assert err < (3e-2 if bf16 else 1e-5)
 
 
 def test_training_reduces_loss(lq):
