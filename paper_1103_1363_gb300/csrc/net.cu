@@ -13,8 +13,9 @@
 // canonical site order.  Inside the network they are planar: per batch item
 // and channel, six float4 planes over the sites, plane q holding complex
 // components 2q and 2q+1 of the 12 values k = 3 spin + colour (a warp's
-// loads of consecutive sites are then one contiguous stretch).  Per hop, the transported inputs of a tile of sites are
-// gathered into shared memory, and the real-ified product
+// loads of consecutive sites are then one contiguous stretch).  Per hop,
+// the transported inputs of a tile of sites are gathered into shared
+// memory, and the real-ified product
 //   OUT[row][n2] += X[row][k2] * B_h[k2][n2]
 // (row = (site, colour), k2 = 2*(ci*4+r) + {re, im}, n2 = 2*(co*4+s) +
 // {re, im}) is accumulated over the nine hops:
@@ -25,6 +26,8 @@
 //   the gather of hop h+1 runs while the MMAs of hop h execute; one thread
 //   issues the MMAs and an mbarrier tracks their completion.
 // - FP32 path: FMAs on 64-site tiles, accumulators in registers.
+// The weight gradient is the same contraction summed over the rows instead
+// (tensor cores for BF16, FMAs for FP32).
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -341,15 +344,15 @@ __device__ __forceinline__ void load_channel(const float* in_b, int V, int ci, i
 
 // BF16 forward of one layer on the tensor cores.  Shared memory: two
 // operand stages, each X (3 colour blocks of 128 sites x K2p) and B_h
-// (N2p x K2p), both BF16 in core-matrix order; two link stages (per site:
-// the hop's link times the boundary sign, and the neighbour); then four
+// (N2p x K2p), both BF16 in core-matrix order; two link stages (per site
+// the hop's link times the boundary sign in 18 floats, plus one float of
+// padding: the odd stride makes the reads conflict-free); then four
 // mbarriers (MMAs of stage s done, B_h of stage s landed) and the
-// tensor-memory address.  The first 128 threads stage hop h+1's links
-// while the others gather hop h (hop 0, the identity, needs none); slot 18
-// of a site's 19 floats is padding (odd stride: conflict-free reads).
-// Tensor memory: the accumulator of colour a in columns [a N2p, (a+1) N2p),
-// lane = site of the tile.  Thread (site sl = tid % 128, group tid / 128)
-// gathers channels group + 4 j; B_h arrives by one bulk copy per hop.
+// tensor-memory address.  Thread (site sl = tid % 128, group grp = tid /
+// 128): group 0 stages hop h+1's links while groups 1-3 gather hop h
+// (channels grp - 1 + 3 j; hop 0, the identity, needs no link).  B_h
+// arrives by one bulk copy per hop.  Tensor memory: the accumulator of
+// colour a in columns [a N2p, (a+1) N2p), lane = site of the tile.
 template <int RECON>
 __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetLayerArgs a)
 {
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
     uint32_t g = 0;       // hops whose MMAs were issued (each commits once to mma_bar[g & 1])
     int copies = 0;       // bulk copies issued (hop g's lands on b_bar[g & 1])
     bool failed = false;
-    // Each gathering thread walks the items (tile, hop h, channel c0 + TG j),
+    // Each gathering thread walks the items (tile, hop h, channel cfirst + TG j),
     // j < nj, and loads one item ahead, so that a load is in flight while the
     // previous item is transported (across the hop barrier and into the next tile).
     const int cfirst = grp - 1;
