@@ -241,6 +241,10 @@ template <int ISBF> struct SpinorHalfIO {
         float n = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; ++k) n = fmaxf(n, fabsf(v[k]));
+        // a site whose largest component is subnormal (below 2^-126) is stored
+        // as zero: 1/n would overflow to infinity and make the site NaN (NaN
+        // itself still propagates, for the solvers' breakdown checks)
+        if (n < 1.17549435e-38f) n = 0.f;
         const float s = n > 0.f ? 1.f / n : 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -573,9 +577,10 @@ __device__ __forceinline__ void clover_apply_site(const void* base, int stride, 
 // block to finish (atomic ticket) adds the partials in block order.  The
 // result never depends on scheduling.
 
+// Block bidx of the nblk blocks that reduce into `result`.
 template <int NV>
 __device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], double* partials, unsigned* ticket,
-                                                      double* result)
+                                                      double* result, int bidx, int nblk)
 {
     __shared__ double sm[32][NV];
     __shared__ bool last;
@@ -594,11 +599,11 @@ __device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], double* p
         for (int k = 0; k < NV; ++k) {
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += sm[w][k];
-            partials[(size_t)blockIdx.x * NV + k] = s;
+            partials[(size_t)bidx * NV + k] = s;
         }
         __threadfence();
         const unsigned t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned)nblk - 1);
     }
     __syncthreads();
     if (!last) return;
@@ -607,7 +612,7 @@ __device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], double* p
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double x = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += vp[(size_t)b * NV + k];
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) x += vp[(size_t)b * NV + k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) sm[warp][k] = x;
@@ -622,6 +627,13 @@ __device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], double* p
         }
         *ticket = 0u;  // ready for the next launch on this slot
     }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], double* partials, unsigned* ticket,
+                                                      double* result)
+{
+    block_reduce_finalize<NV>(v, partials, ticket, result, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // --------------------------------------------------------------- geometry

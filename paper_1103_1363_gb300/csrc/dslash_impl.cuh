@@ -56,6 +56,7 @@ struct DslashArgs {
     int s_den, s_den2;
     const int* skip;         // per rhs: nonzero = converged, do nothing (may be nullptr)
     int sites_per_thread;    // reducing launches: grid of Vh / (block * this); 0 = one wave of blocks
+    int nrhs;                // right-hand sides of the launch (set by the launcher)
 };
 
 // ---- spin projection (1 + S g_mu), S = -1 or +1, onto two colour vectors
@@ -370,27 +371,31 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i,
     }
 }
 
+// One-dimensional grid: block b serves right-hand side b % nrhs and site
+// block b / nrhs, so that the blocks of all right-hand sides for the same
+// sites run together and share each link (and clover) read through L2.
 template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 1 : LQCD_DSLASH_MINB))
     dslash_kernel(const DslashArgs A)
 {
-    const int rhs = blockIdx.y;
+    const int rhs = (int)(blockIdx.x % (unsigned)A.nrhs);
+    const int sb = (int)(blockIdx.x / (unsigned)A.nrhs), nsb = (int)(gridDim.x / (unsigned)A.nrhs);
     if (A.skip && A.skip[rhs]) return;  // uniform over the rhs: no block of it reduces
     double nrm = 0.0;
     if constexpr (RED || EPI == EPI_CG) {
         // grid-stride: the launcher runs one wave of blocks, so that each
         // block's partial sum covers many sites
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.g.Vh; i += gridDim.x * blockDim.x)
+        for (int i = sb * blockDim.x + threadIdx.x; i < A.g.Vh; i += nsb * blockDim.x)
             dslash_site<PG, PS, RECON, DAG, EPI, RED>(A, rhs, i, nrm);
         double v[1] = {nrm};
-        block_reduce_finalize<1>(v, A.partials + rhs * A.part_rs, A.tickets + rhs, A.red + rhs * A.red_rs);
+        block_reduce_finalize<1>(v, A.partials + rhs * A.part_rs, A.tickets + rhs, A.red + rhs * A.red_rs, sb, nsb);
     } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        const int i = sb * blockDim.x + threadIdx.x;
         if (i < A.g.Vh) dslash_site<PG, PS, RECON, DAG, EPI, RED>(A, rhs, i, nrm);
     }
 }
 
-// Launch helper: grid (ceil(Vh / block), nrhs), one site per thread; for
+// Launch helper: ceil(Vh / block) x nrhs blocks, one site per thread; for
 // launches that reduce (fused norms, fused CG update) at most one wave of
 // resident blocks, so that each block's partial sum covers more sites and the
 // deterministic two-stage reduction handles 608 instead of 8192 partials at
@@ -420,8 +425,10 @@ cudaError_t launch_dslash_t(const DslashArgs& A, int nrhs, int block, cudaStream
             gx = wave[bi];
         }
     }
-    dim3 grid(gx, nrhs);
-    dslash_kernel<PG, PS, RECON, DAG, EPI, RED><<<grid, block, 0, s>>>(A);
+    if ((long)gx * nrhs > 0x7fffffffL) return cudaErrorInvalidConfiguration;
+    DslashArgs Ar = A;
+    Ar.nrhs = nrhs;
+    dslash_kernel<PG, PS, RECON, DAG, EPI, RED><<<gx * nrhs, block, 0, s>>>(Ar);
     return cudaGetLastError();
 }
 

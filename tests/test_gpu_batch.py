@@ -60,3 +60,25 @@ def test_twelve_point_sources_24c48():
     for r in (0, 5, 11):
         assert oracle.true_residual(U, A, kappa, srcs[r], xh[r]) <= 1e-10
     assert st["true_residual"] <= 1e-10
+
+
+@pytest.mark.slow
+def test_point_source_fp16_spinors_24c48():
+    """One point source with FP16-spinor inner storage.  Far from the source
+    the iterates' components drop below the smallest normal FP32 number, and
+    the per-site-norm codec used to turn those sites into NaN (breakdown
+    after the first check interval)."""
+    lq = require_cuda()
+    dims = (24, 24, 24, 48)
+    kappa, csw = 0.135, 1.0
+    U = synth.smooth_gauge(dims, 0.5, 4)
+    b = synth.point_source(dims, 0, 0)
+    lat = lq.Lattice(dims, precisions=("f64", "f32", "f16spinors"), stream=torch.cuda.Stream())
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    x = lat.canonical_spinor()
+    rc, st = lat.solve(x, torch.from_numpy(b).cuda(), 1e-10, inner_prec="f16spinors")
+    print("point source, FP16 spinors: %d iters, true residual %.2e" % (st["iterations"], st["true_residual"]))
+    assert rc == 0 and st["true_residual"] <= 1e-10
+    A = oracle.clover(U, kappa, csw)
+    assert oracle.true_residual(U, A, kappa, b, x.cpu().numpy()) <= 1e-10

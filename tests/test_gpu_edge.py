@@ -7,6 +7,8 @@
   to b), so they converge in one iteration (the invariant-subspace case of
   GMRES); CG on the normal equations reaches r = 0 after one iteration and
   must survive the remaining iterations of its check interval (0/0 steps).
+- 16-bit spinor storage with per-site norms keeps sites whose values are
+  subnormal in FP32 from turning into NaN (stored as zero).
 - The smallest lattice (2^4, where x + mu and x - mu coincide) solves to
   1e-10 with every solver, checked by the oracle.  Its rough Haar links make
   the normal equations so ill-conditioned that 16-bit search directions
@@ -69,6 +71,40 @@ def test_plane_wave_source(lq, name, kw):
     assert np.linalg.norm(xg - xstar) / np.linalg.norm(xstar) < 1e-10
     if name.startswith("fg"):  # CG checks its residual only every check_interval iterations
         assert st["iterations"] <= 2, st["iterations"]
+
+
+@pytest.mark.parametrize("prec", ["f16spinors", "bf16spinors", "f16", "bf16"])
+def test_subnormal_sites_in_16bit_spinors(lq, prec):
+    """Per-site-norm codec: a site whose largest component is below the
+    smallest normal FP32 number (2^-126) is stored as zero.  Dividing by
+    its norm overflowed to infinity and made the site NaN, which broke
+    FP16-spinor solves of point sources at 24^3x48.  Normal sites keep
+    16-bit accuracy relative to their own norm, down to 1e-36."""
+    dims = (4, 4, 4, 4)
+    lat = lq.Lattice(dims, precisions=("f64", "f32", prec))
+    b = synth.gaussian_spinor(dims, 76)
+    exps = [0, 5, 10, 20, 30, 36, 39, 41, 43]
+    lt, lz, ly, lx = b.shape[:4]
+    scale = np.empty((lt, lz, ly, lx))
+    for n, idx in enumerate(np.ndindex(lt, lz, ly, lx)):
+        scale[idx] = 10.0 ** -exps[n % len(exps)]
+    b = b * scale[..., None, None]
+    f = lat.new_field(prec)
+    lat.pack(f, b, 1, prec)
+    out = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    lat.unpack(out, f, 1, prec)
+    u = out.cpu().numpy()
+    assert np.all(np.isfinite(u))
+    t, z, y, x = np.indices((lt, lz, ly, lx))
+    odd = ((t + z + y + x) & 1) == 1
+    vmax = np.abs(b).reshape(lt, lz, ly, lx, -1).max(axis=-1)
+    err = np.abs(u - b).reshape(lt, lz, ly, lx, -1).max(axis=-1)
+    tol = 2.0 ** -10 if prec.startswith("f16") else 2.0 ** -7
+    normal = odd & (vmax > 1e-36)
+    tiny = odd & (vmax < 1e-38)
+    assert normal.sum() > 0 and tiny.sum() > 0
+    assert np.all(err[normal] <= tol * vmax[normal])
+    assert np.all(u.reshape(lt, lz, ly, lx, -1)[tiny] == 0)
 
 
 @pytest.mark.parametrize("name,kw", SOLVERS, ids=[s[0] for s in SOLVERS])
