@@ -322,7 +322,9 @@ def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
 
 def run_hop_kernel(args, w):
     """Stand-alone parity hopping term (recon-12) of one precision, for kernel
-    profiles: warmup + steps launches over 8 rotating buffer pairs."""
+    profiles: warmup + steps launches over 8 rotating buffer pairs, each
+    holding --nrhs right-hand sides (one launch serves all of them; the
+    compulsory bytes count the links once per launch)."""
     import torch
 
     import synth
@@ -333,19 +335,25 @@ def run_hop_kernel(args, w):
     lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, stream=stream)
     lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
     b = synth.gaussian_spinor(dims, w["src_seed"])
-    nbuf = 8
+    R = args.nrhs
+    if R > 1:
+        lat.close()
+        lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, max_nrhs=R, stream=stream)
+        lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
+    nbuf = 8 if R == 1 else 3
     with torch.cuda.stream(stream):
-        fins = [lat.new_field(args.prec) for _ in range(nbuf)]
-        fouts = [lat.new_field(args.prec) for _ in range(nbuf)]
+        fins = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
+        fouts = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
+    bb = np.broadcast_to(b, (R,) + b.shape).copy()
     for f in fins:
-        lat.pack(f, b, 1, args.prec)
+        lat.pack(f, bb, 1, args.prec, nrhs=R)
     for i in range(args.warmup):
-        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec)
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec, nrhs=R)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec)
+        lat.dslash(fouts[i % nbuf], fins[i % nbuf], 0, prec=args.prec, nrhs=R)
     e1.record(stream)
     stream.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / args.steps
@@ -355,10 +363,11 @@ def run_hop_kernel(args, w):
             "bf16spinors": 48}
     sb = spinor[args.prec]
     lb = link[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
-    comp = (2 * sb + 8 * lb) * Vh
+    comp = (2 * sb * R + 8 * lb) * Vh
     hb, src = measured_peaks()
-    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "workload": workload_name(w),
-                      "us_per_launch": round(t * 1e6, 2), "gflops": round(1320.0 * Vh / t / 1e9, 1),
+    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "nrhs": R, "workload": workload_name(w),
+                      "us_per_launch": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / R, 2),
+                      "gflops": round(1320.0 * Vh * R / t / 1e9, 1),
                       "compulsory_bytes": comp, "achieved_gbs": round(comp / t / 1e9, 1),
                       "frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": src}), flush=True)
     return 0
@@ -518,6 +527,7 @@ def main():
     ap.add_argument("--nmr", type=int, default=4, help="MR iterations per block of --kernel sap")
     ap.add_argument("--prec", default="f16", help="precision of --kernel hop")
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18], help="link storage of --kernel hop")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch of --kernel hop")
     ap.add_argument("--cpu-applications", type=int, default=3)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
