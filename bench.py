@@ -481,7 +481,7 @@ def oracle_sample(w, napply):
         times.append(time.perf_counter() - t0)
     flops_per = 2 * 1320.0 * (V // 2)
     return {"times": times, "gflops": flops_per * len(times) / sum(times) / 1e9,
-            "cores": os.cpu_count()}
+            "cores": oracle.num_threads()}
 
 
 def run_reference(args, w):

@@ -42,6 +42,7 @@ _L = C.c_long
 _PREC = C.CFUNCTYPE(None, _P, _P, _P)
 
 _SIGS = {
+    "oracle_num_threads": (_I, []),
     "oracle_gamma": (None, [_I, _P]),
     "oracle_sigma": (None, [_I, _I, _P]),
     "oracle_hop": (None, [_P, _I, _P, _P, _P]),
@@ -93,6 +94,11 @@ def use_library(path):
     prev = _lib
     _lib = None if path is None else _load(path)
     return prev
+
+
+def num_threads():
+    """Threads of the oracle's OpenMP loops (the cores a timed run uses)."""
+    return int(lib().oracle_num_threads())
 
 
 def _c(a):

@@ -35,6 +35,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -895,4 +898,15 @@ int oracle_fgcr(const int d[4], int tanti, const cplx *U, const cplx *A, double 
     *true_res = res;
     free(r); free(z); free(w); free(ww);
     return res <= tol ? 0 : 1;
+}
+
+/* Threads an OpenMP loop of this library runs on (1 without OpenMP): the
+ * core count a timed oracle run reports. */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
