@@ -265,10 +265,15 @@ typedef struct lqcd_net lqcd_net;
  * max_batch: largest batch of forward / training calls.  Needs F32 links. */
 lqcd_status lqcd_net_create(lqcd_ctx* ctx, int nlayers, const int* channels, int bf16, int max_batch,
                             lqcd_net** out);
+/* Frees the handle; the caller frees the workspace it provided. */
 lqcd_status lqcd_net_destroy(lqcd_net* net);
+/* Device bytes the network needs: weights, gradients, Adam moments, the
+ * real-ified forward and adjoint weights, activations of every layer
+ * boundary and two gradient buffers for max_batch items, reduction scratch. */
 lqcd_status lqcd_net_workspace_size(const lqcd_net* net, size_t* bytes);
 /* Caller-owned device workspace, 256-byte aligned; weights start at zero. */
 lqcd_status lqcd_net_set_workspace(lqcd_net* net, void* dev_ptr, size_t bytes);
+/* Complex weights in all: the sum over layers of 9 x 4 C_out x 4 C_in. */
 lqcd_status lqcd_net_num_weights(const lqcd_net* net, size_t* complex_count);
 /* w: host or device FP32 complex weights (resets the Adam moments). */
 lqcd_status lqcd_net_set_weights(lqcd_net* net, const float* w);
