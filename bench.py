@@ -460,6 +460,95 @@ def run_sap_kernel(args, w):
     return 0
 
 
+def bf16_peak():
+    """Measured dense BF16 burst peak (TFLOP/s) and its source."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def run_net_kernel(args, w):
+    """The BF16 parallel-transport network of the learned preconditioner on
+    a 16^4 lattice (links exp(i 0.5 H), seed 100), widths 1 -> 12 -> 12 -> 1:
+    the 3-layer forward at batch 1 (one preconditioner application), then at
+    batch --batch the 12 -> 12 layer, its adjoint, its weight gradient and a
+    whole training step.  Each is timed with CUDA events on the context's
+    stream over --steps calls after --warmup; the library's kernel timer
+    (lqcd_net_profile_*) gives the layer kernels' own device time, without
+    the layout conversions at the ABI calls.  Inputs are seeded complex
+    Gaussian activations."""
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import learned, lqcd
+    dims = (16, 16, 16, 16)
+    V = int(np.prod(dims))
+    B = args.batch
+    stream = torch.cuda.Stream()
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32"), stream=stream)
+    lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, 0.5, 100)).cuda())
+    chans = (1, 12, 12, 1)
+    net = lqcd.Net(lat, chans, bf16=True, max_batch=B)
+    net.set_max_ctas(args.max_ctas)
+    net.set_weights(learned.init_weights(chans, 7, scale=0.1))
+    gen = torch.Generator().manual_seed(11)
+
+    def act(ch, batch):
+        return torch.randn((batch, V, ch, 4, 3), dtype=torch.complex64, generator=gen).to("cuda")
+
+    x1, x12, g12 = act(1, B), act(12, B), act(12, B)
+    y1, y12 = torch.empty_like(x1), torch.empty_like(x12)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pk, psrc = bf16_peak()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        stream.synchronize()
+        net.profile_enable(True)
+        net.profile_read()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        prof = net.profile_read()
+        net.profile_enable(False)
+        return e0.elapsed_time(e1) / args.steps, prof
+
+    out = {"kernel": "net", "workload": "parallel-transport network 1-12-12-1, BF16 tensor cores, 16^4, "
+                                        "exp(i 0.5 H) links", "batch": B, "max_ctas": args.max_ctas,
+           "peak_tflops": pk, "peak_source": psrc + " bf16 burst"}
+
+    def kern(prof, key):
+        e = prof[key]
+        if e["launches"] == 0:
+            return None
+        us = 1e3 * e["ms"] / e["launches"]
+        tf = e["flops"] / (e["ms"] * 1e-3) / 1e12
+        return {"launches": e["launches"], "us_per_launch": round(us, 2), "tflops": round(tf, 1),
+                "frac": round(tf / pk, 4), "achieved_gbs": round(e["bytes"] / (e["ms"] * 1e-3) / 1e9, 1)}
+
+    ms, prof = timed(lambda: net.forward(y1[:1], x1[:1], 1))
+    out["forward_batch1"] = {"ms_per_call": round(ms, 4),
+                             "layers": {"%d" % l: kern(prof, (l, "fwd")) for l in range(3)}}
+    ms, prof = timed(lambda: net.layer_apply(1, y12, x12, batch=B))
+    out["layer12"] = dict(kern(prof, (1, "fwd")), ms_per_call_with_conversions=round(ms, 4))
+    ms, prof = timed(lambda: net.layer_apply(1, y12, g12, batch=B, adjoint=True))
+    out["layer12_adjoint"] = dict(kern(prof, (1, "adj")), ms_per_call_with_conversions=round(ms, 4))
+    ms, prof = timed(lambda: net.layer_wgrad(1, x12, g12, batch=B))
+    out["layer12_wgrad"] = dict(kern(prof, (1, "wgrad")), ms_per_call_with_conversions=round(ms, 4))
+    r, e = act(1, B)[:, :, 0], act(1, B)[:, :, 0]
+    r, e = r.contiguous(), e.contiguous()
+    ms, prof = timed(lambda: net.train_step(r, e, B, lr=0.0))
+    out["train_step"] = {"ms_per_step": round(ms, 4),
+                         "kernels": {"%d_%s" % k: kern(prof, k) for k in prof if prof[k]["launches"]}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------ oracle (CPU)
 
 def oracle_sample(w, napply):
@@ -519,9 +608,12 @@ def main():
     ap.add_argument("--inner", default="f16spinors", choices=["f32", "f16", "bf16", "f16links", "bf16links", "f16spinors",
                                                       "bf16spinors"],
                     help="storage of the timed solve's inner iteration")
-    ap.add_argument("--kernel", default=None, choices=["hop", "sap"],
-                    help="instead of the solve: time the stand-alone parity hopping kernel, or the SAP "
-                         "preconditioner and SAP-FGCR (profiling)")
+    ap.add_argument("--kernel", default=None, choices=["hop", "sap", "net"],
+                    help="instead of the solve: time the stand-alone parity hopping kernel, the SAP "
+                         "preconditioner and SAP-FGCR, or the learned preconditioner's network kernels "
+                         "(profiling)")
+    ap.add_argument("--batch", type=int, default=16, help="batch of --kernel net's layer and training timings")
+    ap.add_argument("--max-ctas", type=int, default=0, help="CTA cap of --kernel net (0: one per SM)")
     ap.add_argument("--block", default="4x4x4x4", help="SAP block extents of --kernel sap")
     ap.add_argument("--ncycle", type=int, default=5, help="SAP cycles of --kernel sap")
     ap.add_argument("--nmr", type=int, default=4, help="MR iterations per block of --kernel sap")
@@ -537,6 +629,8 @@ def main():
         return run_hop_kernel(args, w)
     if args.kernel == "sap":
         return run_sap_kernel(args, w)
+    if args.kernel == "net":
+        return run_net_kernel(args, w)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

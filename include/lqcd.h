@@ -38,6 +38,10 @@
  * in one caller-owned workspace (lqcd_workspace_size / lqcd_set_workspace),
  * typically a torch tensor.  Vectors handed to calls are caller-owned too.
  *
+ * Devices: a call that touches the GPU makes the context's device current
+ * while it runs and gives the calling thread its previous current device
+ * back before returning.
+ *
  * Errors: every call returns an lqcd_status and never throws.  A
  * human-readable message for the last failure on the calling thread is
  * available from lqcd_last_error().  Calls are asynchronous on the
@@ -227,11 +231,16 @@ lqcd_status lqcd_solve(lqcd_ctx* ctx, double* x, const double* b, double tol, in
  * the two hopping sweeps lives in a 32 MiB array that the library's CUDA
  * module carries on every GPU that loads it (held until the process exits),
  * not in the context's workspace.  For callers that cannot allocate device
- * memory where they apply the operator.  The paper has no counterpart.
- *   - The call allocates nothing and calls no allocating routine.
+ * memory where they apply the operator: a fixed memory budget, an allocator
+ * that must not grow, or code running where cudaMalloc is not allowed.  The
+ * paper has no counterpart.
+ *   - The call allocates nothing, calls no allocating routine and writes
+ *     nothing in the context's workspace (its solver vectors stay intact).
  *   - Limit: nrhs x lqcd_field_bytes(prec) <= 32 MiB, else LQCD_ERR_INVALID.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call looks up the array's address on the context's device
+ *     (cudaGetSymbolAddress); the first call on a device can load the
+ *     library's module there, so make that first call before any stream
+ *     capture.
  *   - Every call on a device shares the one array: calls that overlap on the
  *     GPU (other streams, other contexts, other threads) race.  Nothing in it
  *     needs clearing: each call overwrites the part it reads.
@@ -273,6 +282,22 @@ lqcd_status lqcd_net_destroy(lqcd_net* net);
 lqcd_status lqcd_net_workspace_size(const lqcd_net* net, size_t* bytes);
 /* Caller-owned device workspace, 256-byte aligned; weights start at zero. */
 lqcd_status lqcd_net_set_workspace(lqcd_net* net, void* dev_ptr, size_t bytes);
+/* Bind the network to another context of the same lattice (extents, t
+ * boundary, recon, device) that holds loaded F32 links: later layers
+ * transport with that context's links and run on its stream; the network's
+ * workspace, weights and Adam state stay.  Training over several gauge fields
+ * keeps one context per field resident and binds instead of reloading links.
+ * LQCD_ERR_INVALID if the lattices differ, LQCD_ERR_STATE without links. */
+lqcd_status lqcd_net_bind(lqcd_net* net, lqcd_ctx* ctx);
+/* Cap the CTAs of the BF16 network's persistent launches: at most max_ctas
+ * CTAs for a layer (forward or adjoint; by default one per SM, each striding
+ * over the batch x 128-site tiles) and at most max_ctas CTAs per hop for the
+ * weight gradient (default SMs / 9); the FP32 weight gradient takes the same
+ * cap per hop.  0 restores the defaults.  Results do not depend on the cap
+ * beyond the FP32 summation order of the weight gradient's atomics; a small
+ * cap makes every CTA run many tiles (tests use it to check the multi-tile
+ * path on small lattices).  LQCD_ERR_INVALID for max_ctas < 0. */
+lqcd_status lqcd_net_set_max_ctas(lqcd_net* net, int max_ctas);
 /* Complex weights in all: the sum over layers of 9 x 4 C_out x 4 C_in. */
 lqcd_status lqcd_net_num_weights(const lqcd_net* net, size_t* complex_count);
 /* w: host or device FP32 complex weights (resets the Adam moments). */
@@ -293,6 +318,19 @@ lqcd_status lqcd_net_forward(lqcd_net* net, float* out, const float* in, int bat
  * step (reading it synchronises the stream). */
 lqcd_status lqcd_net_train_step(lqcd_net* net, const float* r, const float* e, int batch, double lr, double beta1,
                                 double beta2, double eps, double* loss);
+
+/* Training pair of the learned preconditioner: for nrhs canonical FP64
+ * spinors x* (xstar) and x (device pointers, back to back; x = NULL means
+ * x = 0), e = x* - x and r = M e, with M the operator of the last
+ * lqcd_clover_compute.  r and e are written as canonical FP32 complex
+ * spinors (device, nrhs back to back), the network's input and target
+ * layout.  With x the iterate of a solver started from 0 on b = M x*, r is
+ * that solver's residual b - M x and e its error.  M e is applied in FP64
+ * and rounded to FP32 once.  Uses the workspace's solver vectors as scratch
+ * (in chunks of cfg.max_nrhs); asynchronous on the stream.  LQCD_ERR_STATE
+ * without a gauge field and clover term, LQCD_ERR_INVALID for host
+ * pointers. */
+lqcd_status lqcd_training_pair(lqcd_ctx* ctx, float* r, float* e, const double* xstar, const double* x, int nrhs);
 
 /* Right preconditioner of LQCD_SOLVER_FGCR and LQCD_SOLVER_FGMRES_DR (NULL:
  * identity).  The network must belong to this context and outlive its use. */
@@ -377,6 +415,19 @@ typedef struct {
 } lqcd_profile_entry;
 lqcd_status lqcd_profile_enable(lqcd_ctx* ctx, int enable);
 lqcd_status lqcd_profile_read(lqcd_ctx* ctx, lqcd_profile_entry out[LQCD_NPREC]);
+
+/* Kernel timing of a network: while enabled, every layer launch (forward,
+ * adjoint) and weight-gradient launch is bracketed by CUDA events on the
+ * context's stream (not the layout conversions at the ABI calls; graph
+ * replays are not recorded).  lqcd_net_profile_read waits for the stream and
+ * fills out[3 * layer + kind] (kind 0 forward, 1 adjoint, 2 weight gradient;
+ * nentries >= 3 nlayers) with the launches since the last read, their device
+ * time, their compulsory bytes (FP32 input and output activations and each
+ * FP32 link once per item) and the flops of the channel contraction (8 per
+ * complex multiply-add, 4 C_out x 4 C_in x 3 colours x 9 hops per site and
+ * item). */
+lqcd_status lqcd_net_profile_enable(lqcd_net* net, int enable);
+lqcd_status lqcd_net_profile_read(lqcd_net* net, lqcd_profile_entry* out, int nentries);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* lqcd_last_error(void);

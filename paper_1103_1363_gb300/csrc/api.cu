@@ -233,13 +233,6 @@ static lqcd_status check_ready(const lqcd_ctx* c)
     return LQCD_OK;
 }
 
-static lqcd_status set_device_of(const lqcd_ctx* c)
-{
-    int cur = -1;
-    LQ_CUDA(cudaGetDevice(&cur));
-    if (cur != c->device) LQ_CUDA(cudaSetDevice(c->device));
-    return LQCD_OK;
-}
 
 extern "C" {
 
@@ -383,7 +376,8 @@ lqcd_status lqcd_set_workspace(lqcd_ctx* c, void* ptr, size_t bytes)
     cudaPointerAttributes attr;
     LQ_CUDA(cudaPointerGetAttributes(&attr, ptr));
     c->device = attr.device;
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     c->ws = static_cast<char*>(ptr);
     c->ws_bytes = bytes;
     auto at = [&](const lqcd_ctx::Slot& s) -> char* { return s.bytes ? c->ws + s.off : nullptr; };
@@ -425,7 +419,8 @@ lqcd_status lqcd_gauge_load(lqcd_ctx* c, const double* links)
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     if (!links) return fail(LQCD_ERR_INVALID, "lqcd_gauge_load: null links");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     const int Lt = c->g.L[3];
     const size_t per_t = (size_t)c->volume / Lt * 72;  // doubles per t slice
     if (is_device_ptr(links)) {
@@ -456,7 +451,8 @@ lqcd_status lqcd_clover_compute(lqcd_ctx* c, double kappa, double csw)
     LQ_TRY(check_ready(c));
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_clover_compute: no gauge field loaded");
     if (!(kappa > 0.0) || !(csw >= 0.0)) return fail(LQCD_ERR_INVALID, "lqcd_clover_compute: need kappa > 0, csw >= 0");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     c->kappa = kappa;
     c->csw = csw;
     if (csw == 0.0) {
@@ -490,7 +486,8 @@ static lqcd_status pack_common(lqcd_ctx* c, void* internal, double* canonical, i
     if (parity < -1 || parity > 1) return fail(LQCD_ERR_INVALID, "pack: parity must be -1, 0 or 1");
     if (nrhs < 1) return fail(LQCD_ERR_INVALID, "pack: nrhs must be >= 1");
     if (!is_device_ptr(internal)) return fail(LQCD_ERR_INVALID, "pack: internal field must be device memory");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     const size_t canon_rb = (size_t)c->volume * 192;
     const size_t int_rb = (parity < 0 ? 2 : 1) * c->field_bytes(prec);
     if (is_device_ptr(canonical)) {
@@ -544,7 +541,8 @@ lqcd_status lqcd_dslash(lqcd_ctx* c, void* out, const void* in, int parity, doub
     const int op = op_flags & 0xff;
     const bool dag = (op_flags & LQCD_DAG) != 0;
     if ((op_flags & ~(0xff | LQCD_DAG)) != 0 || op > LQCD_OP_FULL) return fail(LQCD_ERR_INVALID, "lqcd_dslash: bad op_flags");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     const size_t fb = c->field_bytes(prec);
     if (op == LQCD_OP_HOP) {
         if (parity != 0 && parity != 1) return fail(LQCD_ERR_INVALID, "lqcd_dslash: parity must be 0 or 1");
@@ -574,6 +572,35 @@ lqcd_status lqcd_dslash(lqcd_ctx* c, void* out, const void* in, int parity, doub
     LQ_GUARD_END
 }
 
+lqcd_status lqcd_training_pair(lqcd_ctx* c, float* r, float* e, const double* xstar, const double* x, int nrhs)
+{
+    LQ_GUARD_BEGIN
+    LQ_TRY(check_ready(c));
+    if (!r || !e || !xstar) return fail(LQCD_ERR_INVALID, "lqcd_training_pair: null field");
+    if (nrhs < 1) return fail(LQCD_ERR_INVALID, "lqcd_training_pair: nrhs must be >= 1");
+    if (!c->gauge_loaded || !c->clover_state)
+        return fail(LQCD_ERR_STATE, "lqcd_training_pair: load the gauge field and call lqcd_clover_compute first");
+    if (!is_device_ptr(r) || !is_device_ptr(e) || !is_device_ptr(xstar) || (x && !is_device_ptr(x)))
+        return fail(LQCD_ERR_INVALID, "lqcd_training_pair: every field must be device memory");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
+    const size_t canon_rb = (size_t)c->volume * 192, canon32_rb = (size_t)c->volume * 96;
+    const size_t full_rb = 2 * c->field_bytes(P64);
+    char* e_int = vec64_field(c, 0, 0);  // max_nrhs full FP64 fields each
+    char* r_int = vec64_field(c, 1, 0);
+    for (int r0 = 0; r0 < nrhs; r0 += c->cfg.max_nrhs) {
+        const int n = nrhs - r0 < c->cfg.max_nrhs ? nrhs - r0 : c->cfg.max_nrhs;
+        const double* xs = xstar + (size_t)r0 * canon_rb / sizeof(double);
+        const double* xx = x ? x + (size_t)r0 * canon_rb / sizeof(double) : nullptr;
+        LQ_TRY(pack_difference(c, e_int, xs, xx, n, full_rb, canon_rb));
+        LQ_TRY(op_full(c, r_int, e_int, P64, false, n, full_rb));
+        LQ_TRY(unpack_spinor_f32(c, e + (size_t)r0 * canon32_rb / sizeof(float), e_int, n, full_rb, canon32_rb));
+        LQ_TRY(unpack_spinor_f32(c, r + (size_t)r0 * canon32_rb / sizeof(float), r_int, n, full_rb, canon32_rb));
+    }
+    return LQCD_OK;
+    LQ_GUARD_END
+}
+
 lqcd_status lqcd_clover_apply(lqcd_ctx* c, void* out, const void* in, int parity, int inverse, lqcd_prec prec, int nrhs)
 {
     LQ_GUARD_BEGIN
@@ -583,7 +610,8 @@ lqcd_status lqcd_clover_apply(lqcd_ctx* c, void* out, const void* in, int parity
     if (parity != 0 && parity != 1) return fail(LQCD_ERR_INVALID, "lqcd_clover_apply: parity must be 0 or 1");
     if (nrhs < 1) return fail(LQCD_ERR_INVALID, "lqcd_clover_apply: nrhs must be >= 1");
     if (!c->clover_state || c->csw == 0.0) return fail(LQCD_ERR_STATE, "lqcd_clover_apply: no clover term computed");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     return clover_apply_launch(c, out, in, parity, inverse ? 1 : 0, prec, nrhs, c->field_bytes(prec));
     LQ_GUARD_END
 }
@@ -592,7 +620,8 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
 {
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     int err = 0;
     LQ_CUDA(cudaMemcpyAsync(&err, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LQ_CUDA(cudaStreamSynchronize(c->stream));
@@ -620,7 +649,8 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
         LQ_TRY(check_prec(c, p.inner_prec));
         memset(&stats[i], 0, sizeof(stats[i]));
     }
-    LQ_TRY(set_device_of(ctxs[0]));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(ctxs[0]->device));
     return solve_batch(ctxs, n, x, b, tol, &p, stats);
     LQ_GUARD_END
 }
@@ -631,7 +661,8 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_s
     LQ_TRY(check_ready(c));
     LQ_TRY(check_prec(c, prec));
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_tune: no gauge field loaded");
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     // scratch: two full fields of the FP64-sized solver vectors, filled with
     // a non-zero byte pattern (finite in every storage format)
     const size_t fb = c->field_bytes(prec);
@@ -739,7 +770,8 @@ lqcd_status lqcd_solve(lqcd_ctx* c, double* x, const double* b, double tol, int 
     if (params) p = *params;
     else lqcd_solver_params_default(&p);
     LQ_TRY(check_prec(c, p.inner_prec));
-    LQ_TRY(set_device_of(c));
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(c->device));
     lqcd_solver_stats st;
     memset(&st, 0, sizeof(st));
     lqcd_status r = solve(c, x, b, tol, nrhs, &p, &st);

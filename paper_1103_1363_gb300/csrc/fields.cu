@@ -44,6 +44,44 @@ __global__ void unpack_kernel(Geom g, int par, double* canon, size_t canon_rb, c
     for (int k = 0; k < 12; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
 }
 
+// FP64 internal field of parity par = canonical a - b (b may be null: 0).
+__global__ void pack_difference_kernel(Geom g, int par, const double* __restrict__ a, const double* __restrict__ b,
+                                       size_t canon_rb, char* out, size_t out_rb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (i >= g.Vh) return;
+    int c[4];
+    cb_coords(g, i, par, c);
+    const size_t off = rhs * canon_rb / sizeof(double) + (size_t)full_index(g, c) * 24;
+    double v[24];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 p = reinterpret_cast<const double2*>(a + off)[k];
+        const double2 q = b ? reinterpret_cast<const double2*>(b + off)[k] : make_double2(0.0, 0.0);
+        v[2 * k] = p.x - q.x;
+        v[2 * k + 1] = p.y - q.y;
+    }
+    SpinorIO<P64>::store(out + rhs * out_rb, g.stride, i, v);
+}
+
+// FP64 internal field of parity par -> canonical FP32 complex spinor.
+__global__ void unpack_f32_kernel(Geom g, int par, float* canon, size_t canon_rb, const char* in, size_t in_rb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (i >= g.Vh) return;
+    int c[4];
+    cb_coords(g, i, par, c);
+    float4* dst = reinterpret_cast<float4*>(reinterpret_cast<char*>(canon) + rhs * canon_rb) +
+                  (size_t)full_index(g, c) * 6;
+    double v[24];
+    SpinorIO<P64>::load(in + rhs * in_rb, g.stride, i, v);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        dst[k] = make_float4((float)v[4 * k], (float)v[4 * k + 1], (float)v[4 * k + 2], (float)v[4 * k + 3]);
+}
+
 // One thread per (checkerboard site, parity, mu) with t0 <= t < t1; the
 // canonical slice starts at site (t0, 0, 0, 0).
 template <int P, int RECON>
@@ -133,6 +171,34 @@ lqcd_status unpack_spinor(lqcd_ctx* c, double* canon, const void* internal, int 
         case P16: unpack_kernel<P16><<<grid, block, 0, c->stream>>>(c->g, par, canon, canon_rb, in, internal_rb); break;
         default: unpack_kernel<PB16><<<grid, block, 0, c->stream>>>(c->g, par, canon, canon_rb, in, internal_rb); break;
         }
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    return LQCD_OK;
+}
+
+lqcd_status pack_difference(lqcd_ctx* c, void* internal, const double* a, const double* b, int nrhs,
+                            size_t internal_rb, size_t canon_rb)
+{
+    const int block = 128;
+    for (int par = 0; par < 2; ++par) {
+        char* out = static_cast<char*>(internal) + par * c->field_bytes(P64);
+        dim3 grid(grid_for(c, block), nrhs);
+        pack_difference_kernel<<<grid, block, 0, c->stream>>>(c->g, par, a, b, canon_rb, out, internal_rb);
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    return LQCD_OK;
+}
+
+lqcd_status unpack_spinor_f32(lqcd_ctx* c, float* canon, const void* internal, int nrhs, size_t internal_rb,
+                              size_t canon_rb)
+{
+    const int block = 128;
+    for (int par = 0; par < 2; ++par) {
+        const char* in = static_cast<const char*>(internal) + par * c->field_bytes(P64);
+        dim3 grid(grid_for(c, block), nrhs);
+        unpack_f32_kernel<<<grid, block, 0, c->stream>>>(c->g, par, canon, canon_rb, in, internal_rb);
         LQ_CUDA(cudaGetLastError());
         c->launches++;
     }

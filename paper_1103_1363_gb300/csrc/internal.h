@@ -29,6 +29,30 @@ lqcd_status cuda_fail(cudaError_t e, const char* where);
         if (s_ != LQCD_OK) return s_;                       \
     } while (0)
 
+// Makes a device current for the lifetime of the object and gives the
+// calling thread its previous current device back on destruction, so that
+// an entry point never leaves the caller on another GPU.
+struct DeviceScope {
+    int prev = -1;
+    lqcd_status enter(int device)
+    {
+        int cur = -1;
+        LQ_CUDA(cudaGetDevice(&cur));
+        if (cur != device) {
+            LQ_CUDA(cudaSetDevice(device));
+            prev = cur;
+        }
+        return LQCD_OK;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope() = default;
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 // device error word bits
 enum { ERRW_CLOVER_SINGULAR = 1, ERRW_BREAKDOWN = 2, ERRW_TIMEOUT = 4 };
 
@@ -145,6 +169,12 @@ lqcd_status pack_spinor(lqcd_ctx* c, void* internal, const double* canon_dev, in
                         size_t internal_rb, size_t canon_rb);
 lqcd_status unpack_spinor(lqcd_ctx* c, double* canon_dev, const void* internal, int parity, int P, int nrhs,
                           size_t internal_rb, size_t canon_rb);
+// full FP64 internal fields = canonical a - b (b null: a); and full FP64
+// internal fields -> canonical FP32 complex spinors
+lqcd_status pack_difference(lqcd_ctx* c, void* internal, const double* a, const double* b, int nrhs,
+                            size_t internal_rb, size_t canon_rb);
+lqcd_status unpack_spinor_f32(lqcd_ctx* c, float* canon, const void* internal, int nrhs, size_t internal_rb,
+                              size_t canon_rb);
 lqcd_status gauge_pack(lqcd_ctx* c, const double* canon_dev_slice, int t0, int t1, int P);
 lqcd_status convert_field(lqcd_ctx* c, void* out, int Pout, const void* in, int Pin, int nrhs, size_t out_rb,
                           size_t in_rb, int nf, int norm_slot /* -1: no norm */);

@@ -996,7 +996,32 @@ __global__ void net_adam_kernel(float* w, float* m, float* v, const float* g, in
 
 using namespace lqcd;
 
+// CUDA-event timing of the layer and weight-gradient launches (while enabled).
+struct NetProfiler {
+    struct Rec { int idx; cudaEvent_t a, b; double bytes, flops; };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    ~NetProfiler()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+        for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    }
+};
+
 struct lqcd_net {
+    NetProfiler* prof;     // null unless lqcd_net_profile_enable was called
     lqcd_ctx* ctx;
     int nlayers;
     int ch[8];             // channels, ch[0] = ch[nlayers] = 1
@@ -1021,6 +1046,7 @@ struct lqcd_net {
     size_t woff[9];        // float offsets of layer weights in W (layer nlayers = total)
     size_t boff[8], bhoff[8];
     long adam_t;
+    int max_ctas;          // cap on the CTAs of the persistent tensor-core launches (0: one per SM)
     size_t nW() const { return woff[nlayers]; }
 };
 
@@ -1082,18 +1108,43 @@ int sm_count()
     return sms;
 }
 
-lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch)
+// Algorithmic work of one layer launch over `batch` items: the channel
+// contraction (8 real flops per complex multiply-add, 4 C_out x 4 C_in x 3
+// colours x 9 hops per site) and the compulsory bytes (input activations,
+// output activations or gradient, each FP32 link once).
+void layer_work(const NetLayerArgs& a, int batch, double& bytes, double& flops)
+{
+    const double V = (double)a.V * batch;
+    flops = 8.0 * (4.0 * a.cout) * (4.0 * a.cin) * 3.0 * 9.0 * V;
+    bytes = 96.0 * (a.cin + a.cout) * V + 4.0 * gauge_link_bytes(P32, 12) * a.V;
+}
+
+// Event pair around one launch when profiling (not while capturing a graph).
+struct NetTimed {
+    lqcd_net* n;
+    NetProfiler::Rec rec{};
+    bool timed = false;
+    lqcd_status begin(lqcd_net* net, int idx, double bytes, double flops);
+    lqcd_status end();
+};
+
+lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch, int prof_idx)
 {
     lqcd_ctx* c = n->ctx;
     NetLayerArgs a = a0;
     a.batch = batch;
+    double wb = 0.0, wf = 0.0;
+    layer_work(a, batch, wb, wf);
+    NetTimed tm;
+    LQ_TRY(tm.begin(n, prof_idx, wb, wf));
     if (n->bf16) {
         // persistent: one CTA per SM strides over the batch x site tiles
         const int sms = sm_count();
         if (sms <= 0) return fail(LQCD_ERR_CUDA, "net layer: no SM count");
         const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
         const size_t sm = layer_smem_tc(a);
-        const int grid = total < sms ? total : sms;
+        int grid = total < sms ? total : sms;
+        if (n->max_ctas > 0 && grid > n->max_ctas) grid = n->max_ctas;
         if (c->cfg.recon == 12) {
             LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             net_layer_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(a);
@@ -1114,7 +1165,7 @@ lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch)
     }
     LQ_CUDA(cudaGetLastError());
     c->launches++;
-    return LQCD_OK;
+    return tm.end();
 }
 
 lqcd_status prep_weights(lqcd_net* n)
@@ -1156,6 +1207,10 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
     const size_t nw = n->woff[layer + 1] - n->woff[layer];
     if (zero) LQ_CUDA(cudaMemsetAsync(gl, 0, nw * 4, c->stream));
     NetLayerArgs a = layer_args(n, layer, false, in, nullptr);
+    double wb = 0.0, wf = 0.0;
+    layer_work(a, batch, wb, wf);
+    NetTimed tm;
+    LQ_TRY(tm.begin(n, 3 * layer + 2, wb, wf));
     if (n->bf16) {
         // tensor cores: one CTA per SM, sms / 9 CTAs per hop, each over a stride of the batch x site tiles
         const int sms = sm_count();
@@ -1167,6 +1222,7 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
         const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
         int per_hop = sms / 9 > 0 ? sms / 9 : 1;
         if (per_hop > total) per_hop = total;
+        if (n->max_ctas > 0 && per_hop > n->max_ctas) per_hop = n->max_ctas;
         size_t sm = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 2 * NTC_TS * 19 * 4 + 16;
         if (sm < (size_t)NTC_MIN_SMEM) sm = NTC_MIN_SMEM;
         dim3 grid(per_hop, 9);
@@ -1179,11 +1235,13 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
         }
         LQ_CUDA(cudaGetLastError());
         c->launches++;
-        return LQCD_OK;
+        return tm.end();
     }
     const size_t sm = (size_t)NET_ROWS * (a.K2p + 4) * 4 + (size_t)NET_ROWS * 8 * a.cout * 4;
     const int ntiles = (a.V + NET_TS - 1) / NET_TS * batch;
-    dim3 grid(ntiles < 2 * 152 ? ntiles : 2 * 152, 9);
+    int gx = ntiles < 2 * 152 ? ntiles : 2 * 152;
+    if (n->max_ctas > 0 && gx > n->max_ctas) gx = n->max_ctas;
+    dim3 grid(gx, 9);
     if (c->cfg.recon == 12) {
         LQ_CUDA(cudaFuncSetAttribute(net_wgrad_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         net_wgrad_kernel<12><<<grid, NET_THREADS, sm, c->stream>>>(a, gout, batch, gl);
@@ -1193,6 +1251,34 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
     }
     LQ_CUDA(cudaGetLastError());
     c->launches++;
+    return tm.end();
+}
+
+lqcd_status NetTimed::begin(lqcd_net* net, int idx, double bytes, double flops)
+{
+    n = net;
+    NetProfiler* pr = n->prof;
+    if (!pr || !pr->on) return LQCD_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LQ_CUDA(cudaStreamIsCapturing(n->ctx->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return LQCD_OK;
+    rec.idx = idx;
+    rec.bytes = bytes;
+    rec.flops = flops;
+    rec.a = pr->get();
+    rec.b = pr->get();
+    if (!rec.a || !rec.b) return fail(LQCD_ERR_CUDA, "net profiler: cudaEventCreate failed");
+    LQ_CUDA(cudaEventRecord(rec.a, n->ctx->stream));
+    timed = true;
+    return LQCD_OK;
+}
+
+lqcd_status NetTimed::end()
+{
+    if (!timed) return LQCD_OK;
+    LQ_CUDA(cudaEventRecord(rec.b, n->ctx->stream));
+    n->prof->pending.push_back(rec);
+    timed = false;
     return LQCD_OK;
 }
 
@@ -1204,7 +1290,7 @@ namespace lqcd {
 lqcd_status net_forward_all(lqcd_net* n, int batch)
 {
     for (int l = 0; l < n->nlayers; ++l)
-        LQ_TRY(run_layer(n, layer_args(n, l, false, n->act[l], n->act[l + 1]), batch));
+        LQ_TRY(run_layer(n, layer_args(n, l, false, n->act[l], n->act[l + 1]), batch, 3 * l));
     return LQCD_OK;
 }
 
@@ -1300,7 +1386,43 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
 
 lqcd_status lqcd_net_destroy(lqcd_net* n)
 {
+    if (n) delete n->prof;
     delete n;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_net_profile_enable(lqcd_net* n, int enable)
+{
+    try {
+        if (!n) return fail(LQCD_ERR_INVALID, "lqcd_net_profile_enable: null network");
+        if (!n->prof) n->prof = new NetProfiler();
+        n->prof->on = enable != 0;
+        return LQCD_OK;
+    } catch (...) {
+        return fail(LQCD_ERR_NOMEM, "lqcd_net_profile_enable: host allocation failed");
+    }
+}
+
+lqcd_status lqcd_net_profile_read(lqcd_net* n, lqcd_profile_entry* out, int nentries)
+{
+    if (!n || !out) return fail(LQCD_ERR_INVALID, "lqcd_net_profile_read: null argument");
+    if (nentries < 3 * n->nlayers) return fail(LQCD_ERR_INVALID, "lqcd_net_profile_read: needs 3 x nlayers entries");
+    for (int i = 0; i < nentries; ++i) out[i] = lqcd_profile_entry{0, 0.0, 0.0, 0.0};
+    if (!n->prof) return LQCD_OK;
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
+    LQ_CUDA(cudaStreamSynchronize(n->ctx->stream));
+    for (auto& r : n->prof->pending) {
+        float ms = 0.f;
+        LQ_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        out[r.idx].launches += 1;
+        out[r.idx].ms += ms;
+        out[r.idx].bytes += r.bytes;
+        out[r.idx].flops += r.flops;
+        n->prof->pool.push_back(r.a);
+        n->prof->pool.push_back(r.b);
+    }
+    n->prof->pending.clear();
     return LQCD_OK;
 }
 
@@ -1317,6 +1439,8 @@ lqcd_status lqcd_net_set_workspace(lqcd_net* n, void* ptr, size_t bytes)
     if (n->ws) return fail(LQCD_ERR_STATE, "lqcd_net_set_workspace: workspace already set");
     if (bytes < n->need) return fail(LQCD_ERR_NOMEM, "lqcd_net_set_workspace: too small");
     if (reinterpret_cast<uintptr_t>(ptr) & 255) return fail(LQCD_ERR_INVALID, "lqcd_net_set_workspace: 256-byte alignment");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     char* base = static_cast<char*>(ptr);
     auto fix = [&](auto*& p) { p = reinterpret_cast<std::remove_reference_t<decltype(p)>>(base + reinterpret_cast<uintptr_t>(p)); };
     fix(n->W); fix(n->gW); fix(n->m1); fix(n->m2);
@@ -1334,6 +1458,32 @@ lqcd_status lqcd_net_set_workspace(lqcd_net* n, void* ptr, size_t bytes)
     return prep_weights(n);
 }
 
+// Transport with another context's links from now on (same lattice).
+lqcd_status lqcd_net_bind(lqcd_net* n, lqcd_ctx* c)
+{
+    if (!n || !c) return fail(LQCD_ERR_INVALID, "lqcd_net_bind: null argument");
+    const lqcd_ctx* o = n->ctx;
+    for (int m = 0; m < 4; ++m)
+        if (c->g.L[m] != o->g.L[m]) return fail(LQCD_ERR_INVALID, "lqcd_net_bind: lattice extents differ");
+    if (c->g.tanti != o->g.tanti || c->cfg.recon != o->cfg.recon)
+        return fail(LQCD_ERR_INVALID, "lqcd_net_bind: boundary condition or link storage differs");
+    if (c->device != o->device) return fail(LQCD_ERR_INVALID, "lqcd_net_bind: contexts on different GPUs");
+    if (!c->ws || !c->holds(P32) || !c->gauge_loaded)
+        return fail(LQCD_ERR_STATE, "lqcd_net_bind: the context needs a workspace and loaded F32 links");
+    n->ctx = c;
+    return LQCD_OK;
+}
+
+// At most max_ctas CTAs per launch of the persistent layer kernel and per hop
+// of the weight-gradient kernels (0: the default, one per SM).
+lqcd_status lqcd_net_set_max_ctas(lqcd_net* n, int max_ctas)
+{
+    if (!n) return fail(LQCD_ERR_INVALID, "lqcd_net_set_max_ctas: null network");
+    if (max_ctas < 0) return fail(LQCD_ERR_INVALID, "lqcd_net_set_max_ctas: max_ctas must be >= 0");
+    n->max_ctas = max_ctas;
+    return LQCD_OK;
+}
+
 // Weights: complex FP32, layer after layer, each [9][4 cout][4 cin] (re, im).
 lqcd_status lqcd_net_num_weights(const lqcd_net* n, size_t* count)
 {
@@ -1345,6 +1495,8 @@ lqcd_status lqcd_net_num_weights(const lqcd_net* n, size_t* count)
 lqcd_status lqcd_net_set_weights(lqcd_net* n, const float* w)
 {
     if (!n || !w || !n->ws) return fail(LQCD_ERR_INVALID, "lqcd_net_set_weights: null argument or no workspace");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     LQ_CUDA(cudaMemcpyAsync(n->W, w, n->nW() * 4, cudaMemcpyDefault, n->ctx->stream));
     LQ_CUDA(cudaMemsetAsync(n->m1, 0, n->nW() * 4, n->ctx->stream));
     LQ_CUDA(cudaMemsetAsync(n->m2, 0, n->nW() * 4, n->ctx->stream));
@@ -1355,6 +1507,8 @@ lqcd_status lqcd_net_set_weights(lqcd_net* n, const float* w)
 lqcd_status lqcd_net_get_weights(const lqcd_net* n, float* w, float* grad)
 {
     if (!n || !n->ws) return fail(LQCD_ERR_INVALID, "lqcd_net_get_weights: no workspace");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     if (w) LQ_CUDA(cudaMemcpyAsync(w, n->W, n->nW() * 4, cudaMemcpyDefault, n->ctx->stream));
     if (grad) LQ_CUDA(cudaMemcpyAsync(grad, n->gW, n->nW() * 4, cudaMemcpyDefault, n->ctx->stream));
     LQ_CUDA(cudaStreamSynchronize(n->ctx->stream));
@@ -1368,9 +1522,11 @@ lqcd_status lqcd_net_layer_apply(lqcd_net* n, int layer, int adjoint, float* out
     if (!n || !n->ws || !out || !in) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_apply: bad argument");
     if (layer < 0 || layer >= n->nlayers || batch < 1 || batch > n->max_batch)
         return fail(LQCD_ERR_INVALID, "lqcd_net_layer_apply: bad layer/batch");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     const NetLayerArgs a = layer_args(n, layer, adjoint != 0, n->gact[0], n->gact[1]);
     LQ_TRY(convert_layout(n, in, n->gact[0], a.cin, batch, true));
-    LQ_TRY(run_layer(n, a, batch));
+    LQ_TRY(run_layer(n, a, batch, 3 * layer + (adjoint ? 1 : 0)));
     return convert_layout(n, n->gact[1], out, a.cout, batch, false);
 }
 
@@ -1381,6 +1537,8 @@ lqcd_status lqcd_net_layer_wgrad(lqcd_net* n, int layer, const float* in, const 
     if (!n || !n->ws || !in || !gout) return fail(LQCD_ERR_INVALID, "lqcd_net_layer_wgrad: bad argument");
     if (layer < 0 || layer >= n->nlayers || batch < 1 || batch > n->max_batch)
         return fail(LQCD_ERR_INVALID, "lqcd_net_layer_wgrad: bad layer/batch");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     LQ_TRY(convert_layout(n, in, n->gact[0], n->ch[layer], batch, true));
     LQ_TRY(convert_layout(n, gout, n->gact[1], n->ch[layer + 1], batch, true));
     return run_wgrad(n, layer, n->gact[0], n->gact[1], batch, zero);
@@ -1392,6 +1550,8 @@ lqcd_status lqcd_net_forward(lqcd_net* n, float* out, const float* in, int batch
 {
     if (!n || !n->ws || !out || !in) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: bad argument");
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: batch out of range");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     LQ_TRY(convert_layout(n, in, n->act[0], 1, batch, true));
     LQ_TRY(net_forward_all(n, batch));
     return convert_layout(n, n->act[n->nlayers], out, 1, batch, false);
@@ -1406,6 +1566,8 @@ lqcd_status lqcd_net_train_step(lqcd_net* n, const float* r, const float* e, int
 {
     if (!n || !n->ws || !r || !e) return fail(LQCD_ERR_INVALID, "lqcd_net_train_step: bad argument");
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_train_step: batch out of range");
+    DeviceScope dev_scope;
+    LQ_TRY(dev_scope.enter(n->ctx->device));
     lqcd_ctx* c = n->ctx;
     const size_t n_per = act_floats(n, 1);
     LQ_TRY(convert_layout(n, r, n->act[0], 1, batch, true));
@@ -1426,7 +1588,7 @@ lqcd_status lqcd_net_train_step(lqcd_net* n, const float* r, const float* e, int
     for (int l = n->nlayers - 1; l >= 0; --l) {
         LQ_TRY(run_wgrad(n, l, n->act[l], n->gact[cur], batch, 1));
         if (l > 0) {
-            LQ_TRY(run_layer(n, layer_args(n, l, true, n->gact[cur], n->gact[1 - cur]), batch));
+            LQ_TRY(run_layer(n, layer_args(n, l, true, n->gact[cur], n->gact[1 - cur]), batch, 3 * l + 1));
             cur = 1 - cur;
         }
     }

@@ -5,8 +5,9 @@ kernels (operator, CG, network forward / backward, Adam).
 
 Pairs (r, e): for a gauge field, draw x* (complex Gaussian), form b = M x*,
 run 20 iterations of CG on the normal equations of M from x = 0 (the
-library's solver, FP32 inner iteration), and keep r = b - M x_20 and
-e = x* - x_20, so that M e = r exactly.  The network N is trained to map r
+library's solver, FP32 inner iteration), and keep e = x* - x_20 and
+r = M e = b - M x_20 (lqcd_training_pair, which also rounds them to the
+network's FP32 layout).  The network N is trained to map r
 to e (loss |N(r) - e|^2 / |e|^2, Adam), i.e. to act as M^{-1} on the
 residuals that plain CG leaves behind, and is then used as the right
 preconditioner of flexible GCR(20).
@@ -71,14 +72,11 @@ def make_pairs(lat, npairs, seed, cg_iters=20, with_start=True, chunk=None):
         x20 = torch.zeros_like(xs)
         lat.solve(x20, b, 1e-30, nrhs=n, raise_on_error=False, solver=lqcd.SOLVER_CG_FULL, inner_prec="f32",
                   maxiter=cg_iters, check_interval=10, reliable_interval=0)
-        mx = torch.empty_like(xs)
-        apply_full_operator(lat, mx, x20, n)
-        R[k:k + n] = (b - mx).to(torch.complex64)
-        E[k:k + n] = (xs - x20).to(torch.complex64)
+        # e = x* - x_20, r = M e: the residual and error of the 20-iteration iterate
+        lqcd.lqcd_training_pair(lat.ctx, R[k:k + n], E[k:k + n], xs, x20, n)
         k += n
-        if with_start:
-            R[k:k + n] = b.to(torch.complex64)
-            E[k:k + n] = xs.to(torch.complex64)
+        if with_start:  # x = 0: e = x*, r = M x* = b
+            lqcd.lqcd_training_pair(lat.ctx, R[k:k + n], E[k:k + n], xs, None, n)
             k += n
     torch.cuda.synchronize(lat.device)
     return R[:k], E[:k]
@@ -87,14 +85,14 @@ def make_pairs(lat, npairs, seed, cg_iters=20, with_start=True, chunk=None):
 def train(net, fields, epochs, batch, lr=1e-3, seed=0, log=None):
     """Adam on mean |N(r) - e|^2 / |e|^2 over shuffled mini-batches.
 
-    fields: list of (links, R, E) with links the canonical FP64 gauge field
-    on the device and R, E its pairs.  The network transports with the links
-    of its lattice, so every mini-batch is drawn from one field and that
-    field is loaded before the step.  Returns the mean loss per epoch."""
+    fields: list of (lat_f, R, E) with lat_f a Lattice holding that gauge
+    field's links (loaded once) and R, E its pairs.  The network transports
+    with the links of the context it is bound to, so every mini-batch is
+    drawn from one field and the network is bound to that field's context
+    (lqcd_net_bind: no links are reloaded).  Mini-batches of all fields are
+    shuffled together.  Returns the mean loss per epoch."""
     gen = torch.Generator(device="cpu").manual_seed(seed)
-    lat = net.lat
     hist = []
-    current = None
     for ep in range(epochs):
         batches = []
         for f, (_, R, _) in enumerate(fields):
@@ -105,10 +103,9 @@ def train(net, fields, epochs, batch, lr=1e-3, seed=0, log=None):
         tot = 0.0
         for j in order:
             f, idx = batches[j]
-            links, R, E = fields[f]
-            if current != f:
-                lat.gauge_load(links)
-                current = f
+            lat_f, R, E = fields[f]
+            if net.bound is not lat_f:
+                net.bind(lat_f)
             idx = idx.to(R.device)
             tot += net.train_step(R.index_select(0, idx).contiguous(), E.index_select(0, idx).contiguous(),
                                   batch, lr=lr)
@@ -160,7 +157,10 @@ def run_experiment(dims=(16, 16, 16, 16), eps=0.5, kappa=0.134, csw=1.0, train_s
         lat.gauge_load(U)
         lat.clover_compute(kappa, csw)
         R, E = make_pairs(lat, n, seed=10000 + s)
-        fields.append((U, R, E))
+        # the field's links stay resident in a small context of their own
+        lat_f = lqcd.Lattice(dims, precisions=("f64", "f32"), max_nrhs=1, device=device)
+        lat_f.gauge_load(U)
+        fields.append((lat_f, R, E))
     t_pairs = time.perf_counter() - t0
     log("pairs: %d in %.1f s" % (sum(per), t_pairs))
     net = lqcd.Net(lat, channels, bf16=True, max_batch=batch)
@@ -168,8 +168,12 @@ def run_experiment(dims=(16, 16, 16, 16), eps=0.5, kappa=0.134, csw=1.0, train_s
     net.set_weights(w0)
     t0 = time.perf_counter()
     hist = train(net, fields, epochs, batch, lr=lr, log=log)
+    torch.cuda.synchronize(device)
     t_train = time.perf_counter() - t0
+    net.bind(lat)
     w_trained = net.get_weights()
+    for lat_f, _, _ in fields:
+        lat_f.close()
     del fields
     results = []
     for s in test_seeds:

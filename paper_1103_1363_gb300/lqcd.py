@@ -87,6 +87,7 @@ _SIGS = {
     "lqcd_profile_read": [_P, C.POINTER(lqcd_profile_entry)],
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
+    "lqcd_training_pair": [_P, _P, _P, _P, _P, _I],
     "lqcd_set_preconditioner_sap": [_P, _P, _I, _I],
     "lqcd_harmonic_ritz": [_I, _P, _I, _I, _P, _P],
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
@@ -98,6 +99,10 @@ _SIGS = {
     "lqcd_net_workspace_size": [_P, C.POINTER(_S)],
     "lqcd_net_set_workspace": [_P, _P, _S],
     "lqcd_net_num_weights": [_P, C.POINTER(_S)],
+    "lqcd_net_set_max_ctas": [_P, _I],
+    "lqcd_net_bind": [_P, _P],
+    "lqcd_net_profile_enable": [_P, _I],
+    "lqcd_net_profile_read": [_P, C.POINTER(lqcd_profile_entry), _I],
     "lqcd_net_set_weights": [_P, _P],
     "lqcd_net_get_weights": [_P, _P, _P],
     "lqcd_net_layer_apply": [_P, _I, _I, _P, _P, _I],
@@ -232,6 +237,12 @@ def lqcd_dslash_schur_static(ctx, out, inp, kappa, csw, dag, prec, nrhs=1):
            "lqcd_dslash_schur_static")
 
 
+def lqcd_training_pair(ctx, r, e, xstar, x=None, nrhs=1):
+    """e = x* - x, r = M e as canonical FP32 complex spinors (device)."""
+    _check(_lib.lqcd_training_pair(ctx, _ptr(r), _ptr(e), _ptr(xstar), _ptr(x) if x is not None else None,
+                                   int(nrhs)), "lqcd_training_pair")
+
+
 def lqcd_clover_apply(ctx, out, inp, parity, inverse, prec, nrhs=1):
     _check(_lib.lqcd_clover_apply(ctx, _ptr(out), _ptr(inp), int(parity), int(inverse),
                                   PREC.get(prec, prec), int(nrhs)), "lqcd_clover_apply")
@@ -343,6 +354,7 @@ class Net:
 
     def __init__(self, lat, channels=(1, 12, 12, 1), bf16=True, max_batch=1):
         self.lat = lat
+        self.bound = lat
         self.channels = tuple(int(c) for c in channels)
         arr = (C.c_int * len(self.channels))(*self.channels)
         h = C.c_void_p()
@@ -368,6 +380,27 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def bind(self, lat):
+        """Transport with lat's links from now on (same lattice as the network's)."""
+        _check(_lib.lqcd_net_bind(self.h, lat.ctx), "lqcd_net_bind")
+        self.bound = lat
+
+    def set_max_ctas(self, max_ctas):
+        """Cap the CTAs of the persistent BF16 launches (0: one per SM)."""
+        _check(_lib.lqcd_net_set_max_ctas(self.h, int(max_ctas)), "lqcd_net_set_max_ctas")
+
+    def profile_enable(self, enable=True):
+        _check(_lib.lqcd_net_profile_enable(self.h, int(bool(enable))), "lqcd_net_profile_enable")
+
+    def profile_read(self):
+        """{(layer, kind): {launches, ms, bytes, flops}}, kind 'fwd', 'adj' or 'wgrad'."""
+        n = 3 * (len(self.channels) - 1)
+        arr = (lqcd_profile_entry * n)()
+        _check(_lib.lqcd_net_profile_read(self.h, arr, n), "lqcd_net_profile_read")
+        kinds = ("fwd", "adj", "wgrad")
+        return {(i // 3, kinds[i % 3]): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
+                                         "flops": arr[i].flops} for i in range(n)}
 
     def use_as_preconditioner(self, enable=True):
         """Make this network the FGCR right preconditioner of its lattice."""

@@ -140,6 +140,20 @@ def unit_gauge(dims):
     return u
 
 
+def constant_abelian_gauge(dims, mu, nu, k):
+    """U_nu(x) = exp(i theta x_mu T) with T = diag(1, -1, 0) and theta =
+    2 pi k / L_mu; every other link is 1 (a constant abelian field strength
+    in the mu-nu plane)."""
+    lt, lz, ly, lx = lattice_shape(dims)
+    u = unit_gauge(dims)
+    theta = 2.0 * np.pi * k / dims[mu]
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    ph = np.exp(1j * theta * [x, y, z, t][mu])
+    u[..., nu, 0, 0] = ph
+    u[..., nu, 1, 1] = ph.conj()
+    return u
+
+
 def gauge_field(dims, kind, seed, eps=None):
     """``kind`` is 'haar', 'smooth' (needs eps) or 'unit'."""
     if kind == "haar":

@@ -122,3 +122,53 @@ def test_smallest_lattice(lq, name, kw):
     assert rc == 0
     assert oracle.true_residual(U, A, kappa, b, x.cpu().numpy()) <= 1e-10
     assert st["precision_fallback"] == (1 if "f16" in name else 0)
+
+
+def test_singular_clover_block_reported(lq):
+    """csw = 1 / (kappa sin theta) in a constant abelian field makes the clover
+    matrix singular on every site (the oracle's inverse reports all of them,
+    tests/test_oracle_pins.py); lqcd_clover_compute returns
+    LQCD_ERR_CLOVER_SINGULAR and lqcd_sync reports it too.  At 90 % of that
+    csw the build succeeds and A^{-1} matches the oracle."""
+    dims = (4, 4, 6, 8)
+    U = synth.constant_abelian_gauge(dims, 0, 1, 1)
+    kappa = 0.13
+    csw = 1.0 / (kappa * np.sin(2 * np.pi / dims[0]))
+    lat = lq.Lattice(dims, precisions=("f64", "f32"))
+    lat.gauge_load(U)
+    with pytest.raises(lq.LqcdError) as e:
+        lat.clover_compute(kappa, csw)
+    assert e.value.status == 8
+    with pytest.raises(lq.LqcdError) as e:
+        lat.sync()
+    assert e.value.status == 8
+    lat.clover_compute(kappa, 0.9 * csw)
+    lat.sync()
+    psi = synth.gaussian_spinor(dims, 77)
+    fin, fout = lat.new_field("f64"), lat.new_field("f64")
+    lat.pack(fin, psi, 1, "f64")
+    lat.clover_apply(fout, fin, 1, True, prec="f64")
+    out = lat.canonical_spinor()
+    lat.unpack(out, fout, 1, "f64")
+    torch.cuda.synchronize()
+    Ainv, bad = oracle.invert_site_matrices(oracle.clover(U, kappa, 0.9 * csw))
+    assert bad == 0
+    t, z, y, x = np.indices(dims[::-1])
+    odd = (((t + z + y + x) & 1) == 1)[..., None, None]
+    want = oracle.apply_site_matrices(Ainv, np.where(odd, psi, 0))
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+
+
+def test_entry_points_restore_the_current_device(lq):
+    """Every call makes the context's device current and then gives the
+    caller's current device back (needs two GPUs to observe)."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU: the context's device is always the current one")
+    dims = (4, 4, 4, 4)
+    lat = lq.Lattice(dims, device="cuda:1", precisions=("f64", "f32"))
+    torch.cuda.set_device(0)
+    lat.gauge_load(synth.smooth_gauge(dims, 0.5, 78))
+    assert torch.cuda.current_device() == 0
+    lat.clover_compute(0.13, 1.0)
+    assert torch.cuda.current_device() == 0

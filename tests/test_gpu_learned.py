@@ -31,6 +31,37 @@ def test_pairs_satisfy_m_e_equals_r():
         assert np.linalg.norm(r) > 0
 
 
+def test_training_pair_matches_oracle():
+    """lqcd_training_pair: e = x* - x and r = M e (FP64, rounded to FP32 once)
+    against the oracle's operator, over more right-hand sides than the
+    context's solver vectors hold (chunked), and with x = 0 (r = M x*)."""
+    lq = require_cuda()
+    dims = (4, 4, 6, 8)
+    kappa, csw = 0.13, 1.0
+    U = synth.smooth_gauge(dims, 0.5, 6)
+    lat = lq.Lattice(dims, max_nrhs=2, precisions=("f64", "f32"))
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    n = 5
+    xs = synth.gaussian_spinor(dims, 20, nfields=n)
+    x = synth.gaussian_spinor(dims, 21, nfields=n)
+    A = oracle.clover(U, kappa, csw)
+    shape = (n,) + xs.shape[1:]
+    for xx in (x, None):
+        R = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        E = torch.empty_like(R)
+        lq.lqcd_training_pair(lat.ctx, R, E, torch.from_numpy(xs).cuda(),
+                              None if xx is None else torch.from_numpy(xx).cuda(), n)
+        torch.cuda.synchronize()
+        for i in range(n):
+            e_want = xs[i] - (0 if xx is None else xx[i])
+            r_want = oracle.wilson_clover(U, A, kappa, e_want)
+            e_got = E[i].cpu().numpy().astype(np.complex128)
+            r_got = R[i].cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(e_got - e_want) / np.linalg.norm(e_want) < 1e-7
+            assert np.linalg.norm(r_got - r_want) / np.linalg.norm(r_want) < 1e-7
+
+
 def test_trained_net_reduces_fgcr_iterations():
     require_cuda()
     from paper_1103_1363_gb300 import learned

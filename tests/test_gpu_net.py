@@ -3,9 +3,19 @@ oracle: each layer, its adjoint (input gradient) and its weight gradient;
 the whole-network gradient of a training step against oracle backprop.
 
 Tolerances: FP32 path rel-L2 <= 1e-5 (FP32 rounding of sums of ~900
-terms); BF16 tensor-core path (forward, adjoint and weight gradient)
-<= 2e-2 (8-bit mantissa operands, FP32 accumulation) and its error is
-printed."""
+terms).  BF16 tensor-core path: each operand is rounded to an 8-bit
+significand (unit roundoff 2^-9 = 2.0e-3) and the products are summed in
+FP32, so a layer's output, input gradient and weight gradient carry a
+relative error of about 2^-9 (measured 2.3e-3 on every case here); the
+tolerance is 5e-3 for one layer and 6e-3 for a training step's gradient,
+which chains five BF16 contractions (measured 2.5e-3).
+
+The persistent BF16 kernels stride over 128-site tiles (one CTA per SM;
+SMs / 9 CTAs per hop for the weight gradient).  Cases with a CTA cap
+(lqcd_net_set_max_ctas) and the 8^4 x 16 batch make every CTA run several
+tiles, so the next-tile prefetch, the mbarrier phases across tiles and the
+weight gradient's accumulation in tensor memory across tiles are compared
+with the oracle too."""
 import numpy as np
 import pytest
 import torch
@@ -40,29 +50,42 @@ def lq():
     return require_cuda()
 
 
-def make(lq, channels, bf16, U, max_batch=2, dims=DIMS):
+TOL_BF16_LAYER = 5e-3
+TOL_BF16_STEP = 6e-3
+
+
+def make(lq, channels, bf16, U, max_batch=2, dims=DIMS, max_ctas=0):
     lat = lq.Lattice(dims, max_nrhs=1)
     lat.gauge_load(U)
     net = lq.Net(lat, channels, bf16=bf16, max_batch=max_batch)
+    net.set_max_ctas(max_ctas)
     return lat, net
 
 
+# (dims, channels, bf16, batch, CTA cap)
 # 4x4x6x8: 768 sites, six full 128-site tiles of the tensor-core kernel;
 # 4x4x6x6: 576 sites, a ragged last tile (64 sites); 2x2x2x2: one tile
 # that is mostly padding; odd widths exercise the K and N padding.
-CASES = [(DIMS, (1, 12, 12, 1), False), (DIMS, (1, 12, 12, 1), True), ((4, 4, 6, 6), (1, 12, 12, 1), True),
-         ((2, 2, 2, 2), (1, 5, 3, 1), True)]
+# Multi-tile cases: cap 1 puts all 12 tiles (batch 2) through one CTA per
+# launch (per hop for the weight gradient); cap 3 on 4x4x6x6 gives each CTA
+# 3-4 tiles with ragged tiles inside its loop; 8^4 x 16 is 512 tiles at the
+# default grid: >= 3 per layer CTA and 32 per weight-gradient CTA.
+CASES = [(DIMS, (1, 12, 12, 1), False, 2, 0), (DIMS, (1, 12, 12, 1), True, 2, 0),
+         ((4, 4, 6, 6), (1, 12, 12, 1), True, 2, 0), ((2, 2, 2, 2), (1, 5, 3, 1), True, 2, 0),
+         (DIMS, (1, 12, 12, 1), True, 2, 1), ((4, 4, 6, 6), (1, 12, 12, 1), True, 2, 3),
+         (DIMS, (1, 12, 12, 1), False, 2, 1), ((8, 8, 8, 8), (1, 12, 12, 1), True, 16, 0)]
+CASE_IDS = ["f32", "bf16", "bf16-ragged", "bf16-tiny-odd", "bf16-1cta", "bf16-ragged-3cta", "f32-1cta",
+            "bf16-8c8-batch16"]
 
 
-@pytest.mark.parametrize("dims,chans,bf16", CASES, ids=["f32", "bf16", "bf16-ragged", "bf16-tiny-odd"])
-def test_layers_forward_adjoint_wgrad(lq, dims, chans, bf16):
+@pytest.mark.parametrize("dims,chans,bf16,B,cap", CASES, ids=CASE_IDS)
+def test_layers_forward_adjoint_wgrad(lq, dims, chans, bf16, B, cap):
     U = synth.smooth_gauge(dims, 0.5, 31)
     rng = np.random.default_rng(0)
     Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
-    lat, net = make(lq, chans, bf16, U, dims=dims)
+    lat, net = make(lq, chans, bf16, U, dims=dims, max_batch=B, max_ctas=cap)
     net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
-    tol = 2e-2 if bf16 else 1e-5
-    B = 2
+    tol = TOL_BF16_LAYER if bf16 else 1e-5
     for l in range(3):
         cin, cout = chans[l], chans[l + 1]
         x = field(dims, cin, 40 + l, B)
@@ -85,13 +108,14 @@ def test_layers_forward_adjoint_wgrad(lq, dims, chans, bf16):
         assert e1 < tol and e2 < tol and e3 < tol
 
 
-@pytest.mark.parametrize("bf16", [False, True])
-def test_train_step_gradient_matches_oracle_backprop(lq, bf16):
+@pytest.mark.parametrize("bf16,cap", [(False, 0), (True, 0), (True, 1), (True, 2)],
+                         ids=["f32", "bf16", "bf16-1cta", "bf16-2cta"])
+def test_train_step_gradient_matches_oracle_backprop(lq, bf16, cap):
     U = synth.smooth_gauge(DIMS, 0.5, 32)
     rng = np.random.default_rng(1)
     chans = (1, 4, 3, 1)
     Ws = [rand_w(rng, chans[l + 1], chans[l]) for l in range(3)]
-    lat, net = make(lq, chans, bf16, U, max_batch=2)
+    lat, net = make(lq, chans, bf16, U, max_batch=2, max_ctas=cap)
     net.set_weights(np.concatenate([w.reshape(-1) for w in Ws]))
     B = 2
     r = field(DIMS, 1, 60, B)
@@ -108,7 +132,7 @@ def test_train_step_gradient_matches_oracle_backprop(lq, bf16):
     y = acts[-1]
     en2 = np.array([np.sum(np.abs(e[b]) ** 2) for b in range(B)])
     want_loss = np.mean([np.sum(np.abs(y[b] - e[b]) ** 2) / en2[b] for b in range(B)])
-    assert abs(loss - want_loss) / want_loss < (2e-2 if bf16 else 1e-5)
+    assert abs(loss - want_loss) / want_loss < (TOL_BF16_STEP if bf16 else 1e-5)
     g = np.stack([2 * (y[b] - e[b]) / (B * en2[b]) for b in range(B)])
     want = []
     for l in range(2, -1, -1):
@@ -117,7 +141,7 @@ def test_train_step_gradient_matches_oracle_backprop(lq, bf16):
     want = np.concatenate([w.reshape(-1) for w in want])
     err = rel(grad.numpy(), want)
     print("train-step gradient rel err %.2e (bf16=%d)" % (err, bf16))
-    assert err < (3e-2 if bf16 else 1e-5)
+    assert err < (TOL_BF16_STEP if bf16 else 1e-5)
 
 
 def test_training_reduces_loss(lq):

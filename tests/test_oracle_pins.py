@@ -285,6 +285,23 @@ def test_clover_constant_abelian_field(mu, nu, k):
         assert abs(A[0, 0, 0, 0, 0, 0] - (1 - kappa * csw * np.sin(theta))) < 1e-14
 
 
+def test_clover_singular_at_kappa_csw_sin_theta_one():
+    """In the constant abelian field A = 1 - kappa csw sin(theta) sigma (x) T
+    has the eigenvalue 1 - kappa csw sin(theta) (sigma and T both have the
+    eigenvalue 1), so csw = 1 / (kappa sin theta) makes every site's clover
+    matrix singular; the oracle's inverse reports every site, and none at
+    90 % of that csw."""
+    dims = (4, 4, 6, 8)
+    U = synth.constant_abelian_gauge(dims, 0, 1, 1)
+    theta = 2 * np.pi / dims[0]
+    kappa = 0.13
+    csw = 1.0 / (kappa * np.sin(theta))
+    _, bad = oracle.invert_site_matrices(oracle.clover(U, kappa, csw))
+    assert bad == int(np.prod(dims))
+    _, bad = oracle.invert_site_matrices(oracle.clover(U, kappa, 0.9 * csw))
+    assert bad == 0
+
+
 def test_field_strength_properties():
     dims = (4, 4, 4, 4)
     U = synth.smooth_gauge(dims, 0.5, 61)
