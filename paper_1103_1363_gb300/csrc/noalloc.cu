@@ -1,16 +1,15 @@
 // Schur-operator application whose scratch lives in a fixed device array.
 //
 // The even-odd Schur operator needs an even-parity intermediate field
-// between its two hopping sweeps.  lqcd_dslash takes it from the context's
-// workspace; lqcd_dslash_schur_static takes it from the array below, which
-// the CUDA module carries in every GPU that loads the library, so the call
-// needs no device memory beyond its inputs and outputs.  It is for callers
-// that cannot allocate device memory where they apply the operator (a
-// fixed memory budget, an allocator that must not grow, code running where
-// cudaMalloc is not allowed) and that set their context up without room for
-// solver vectors.
-#include <mutex>
-
+// between its two hopping sweeps.  lqcd_dslash takes it from the solver
+// vectors of the context's workspace; lqcd_dslash_schur_static takes it from
+// the array below, which the CUDA module carries in every GPU that loads the
+// library.  The call allocates nothing and leaves the workspace untouched,
+// so it can run between the steps of a caller's own solver without
+// clobbering the library's solver vectors.  It is for callers that cannot
+// allocate device memory where they apply the operator: a fixed memory
+// budget, an allocator that must not grow, or code running where cudaMalloc
+// is not allowed.
 #include "internal.h"
 
 namespace lqcd {
@@ -20,23 +19,17 @@ namespace lqcd {
 static constexpr size_t STATIC_SCRATCH_BYTES = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_schur_scratch[STATIC_SCRATCH_BYTES];
 
-// Device address of g_schur_scratch, looked up once per device.  In host
-// code the symbol is only a host-side stand-in; kernels must be given the
-// address cudaGetSymbolAddress returns for the current device.
-static std::mutex g_scratch_mutex;
-static void* g_scratch_ptr[64];
-
-static lqcd_status static_scratch(int device, void** out)
+// Device address of g_schur_scratch on the current device.  In host code
+// the symbol is only a host-side stand-in; kernels must be given the address
+// cudaGetSymbolAddress returns.  It is looked up on every call (cheap once
+// the module is loaded on the device), so that no address outlives a device
+// reset or a recreated primary context.
+static lqcd_status static_scratch(void** out)
 {
-    if (device < 0 || device >= 64) return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: device id out of range");
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_schur_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_schur_scratch)");
-        g_scratch_ptr[device] = p;
-    }
-    *out = g_scratch_ptr[device];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_schur_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_schur_scratch)");
+    *out = p;
     return LQCD_OK;
 }
 
@@ -63,11 +56,10 @@ extern "C" lqcd_status lqcd_dslash_schur_static(lqcd_ctx* c, void* out, const vo
         const size_t fb = c->field_bytes(prec);
         if ((size_t)nrhs * fb > STATIC_SCRATCH_BYTES)
             return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: nrhs x (V/2 field) exceeds the 32 MiB static scratch");
-        int cur = -1;
-        LQ_CUDA(cudaGetDevice(&cur));
-        if (cur != c->device) LQ_CUDA(cudaSetDevice(c->device));
+        DeviceScope dev_scope;
+        LQ_TRY(dev_scope.enter(c->device));
         void* scratch = nullptr;
-        LQ_TRY(static_scratch(c->device, &scratch));
+        LQ_TRY(static_scratch(&scratch));
         const double saved = c->kappa;
         c->kappa = kappa;
         // the first sweep writes every even site of the intermediate before the
