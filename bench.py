@@ -239,6 +239,12 @@ def run_ours(args, w, rank, world, local_rank):
         out["solve"] = compare_solves(lat, bd, xd, stream, params)
         out["dslash_f32"] = dslash_microbench(lat, b, dims, stream, hb, hbsrc)
     lat.close()
+    if rank == 0 and not args.quick:
+        del bd, xd
+        torch.cuda.empty_cache()
+        out["multi_rhs"] = multi_rhs_leg(dev)
+        if not args.skip_learned:
+            out["learned"] = learned_leg(dev)
     return out
 
 
@@ -289,6 +295,131 @@ def compare_solves(lat, bd, xd, stream, params):
     for k in res:
         res[k]["speedup_vs_f64_cg"] = round(f64 / res[k]["seconds"], 2)
     return res
+
+
+def timed_solves(lat, stream, calls):
+    """Run calls() (a list of (x, b, kw) solves) once for warm-up and once
+    timed with CUDA events on the context stream; returns seconds and the
+    stats of the timed solves."""
+    import torch
+    for x, bb, kw in calls:
+        lat.solve(x, bb, TOL, raise_on_error=False, **kw)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sts = []
+    for x, bb, kw in calls:
+        rc, st = lat.solve(x, bb, TOL, raise_on_error=False, **kw)
+        st["status"] = rc
+        sts.append(st)
+    e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) * 1e-3, sts
+
+
+def multi_rhs_leg(dev):
+    """The 12 point sources (every spin and colour at the origin) on 24^3x48,
+    links exp(i 0.5 H) (seed 4), kappa 0.135, csw 1: one multi-right-hand-side
+    solve (FP16 spinors, FP32 links and FP32 inner, FP64 reliable updates,
+    graph replay) against 12 single-source solves of the same kind and 12
+    plain FP64 GPU CG solves; every solve to true residual 1e-10.  Then the
+    uneven batch 8^4 (kappa 0.12) + 12^4 (0.1275) + 16^3x32 (0.135) in one
+    graph-captured lqcd_solve_batch against the three solved one after the
+    other."""
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import lqcd
+    dims = (24, 24, 24, 48)
+    kappa, csw = 0.135, 1.0
+    stream = torch.cuda.Stream(device=dev)
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32"), max_nrhs=12, device=dev, stream=stream)
+    lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, 0.5, 4)).to(dev))
+    lat.clover_compute(kappa, csw)
+    srcs = np.stack([synth.point_source(dims, s, c) for s in range(4) for c in range(3)])
+    b = torch.from_numpy(srcs).to(dev)
+    x = torch.zeros_like(b)
+    res = {"workload": "12 point sources, 24x24x24x48, exp(i 0.5 H) links, kappa 0.135, csw 1.0, tol 1e-10"}
+    mixed = dict(reliable_interval=50, check_interval=10, use_graph=1)
+
+    def summary(t, sts):
+        return {"seconds": round(t, 4), "iterations_max": max(s["iterations"] for s in sts),
+                "true_residual_max": max(s["true_residual"] for s in sts),
+                "all_converged": all(s["status"] == 0 for s in sts),
+                "launches": sum(s["kernel_launches"] for s in sts)}
+
+    for name, kw in (("multi_rhs_f16spinors", dict(mixed, inner_prec="f16spinors")),
+                     ("multi_rhs_f32", dict(mixed, inner_prec="f32"))):
+        t, sts = timed_solves(lat, stream, [(x, b, dict(kw, nrhs=12))])
+        res[name] = summary(t, sts)
+    for name, kw in (("single_rhs_f16spinors_x12", dict(mixed, inner_prec="f16spinors")),
+                     ("plain_f64_cg_x12", dict(inner_prec="f64", check_interval=10))):
+        t, sts = timed_solves(lat, stream, [(x[r], b[r], kw) for r in range(12)])
+        res[name] = summary(t, sts)
+    f64 = res["plain_f64_cg_x12"]["seconds"]
+    for k in list(res):
+        if isinstance(res[k], dict):
+            res[k]["speedup_vs_f64_cg"] = round(f64 / res[k]["seconds"], 2)
+    lat.close()
+    del x, b
+
+    specs = [((8, 8, 8, 8), 0.120, 4), ((12, 12, 12, 12), 0.1275, 5), ((16, 16, 16, 32), 0.135, 6)]
+    lats, xs, bs = [], [], []
+    for d, kap, seed in specs:
+        l = lqcd.Lattice(d, precisions=("f64", "f32"), device=dev, stream=stream)
+        l.gauge_load(torch.from_numpy(synth.smooth_gauge(d, 0.5, seed)).to(dev))
+        l.clover_compute(kap, 1.0)
+        lats.append(l)
+        bs.append(torch.from_numpy(synth.gaussian_spinor(d, seed + 100)).to(dev))
+        xs.append(torch.zeros_like(bs[-1]))
+    p = lqcd.solver_params(inner_prec="f32", use_graph=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ub = {"lattices": ["%dx%dx%dx%d kappa %.4g" % (d + (k,)) for d, k, _ in specs]}
+    for rep in range(2):  # warm-up, timed
+        stream.synchronize()
+        e0.record(stream)
+        rc, st = lqcd.lqcd_solve_batch([l.ctx for l in lats], xs, bs, [TOL] * 3, p, raise_on_error=False)
+        e1.record(stream)
+        stream.synchronize()
+    ub["batch_one_graph"] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "status": rc,
+                             "iterations": [s["iterations"] for s in st],
+                             "true_residual": [s["true_residual"] for s in st],
+                             "launches": sum(s["kernel_launches"] for s in st)}
+    seq = []
+    for rep in range(2):
+        stream.synchronize()
+        e0.record(stream)
+        seq = [l.solve(xx, bb, TOL, raise_on_error=False, inner_prec="f32", use_graph=1)[1]
+               for l, xx, bb in zip(lats, xs, bs)]
+        e1.record(stream)
+        stream.synchronize()
+    ub["one_after_the_other"] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4),
+                                 "iterations": [s["iterations"] for s in seq],
+                                 "seconds_each": [round(s["seconds"], 4) for s in seq],
+                                 "true_residual": [s["true_residual"] for s in seq],
+                                 "launches": sum(s["kernel_launches"] for s in seq)}
+    for l in lats:
+        l.close()
+    res["uneven_batch"] = ub
+    return res
+
+
+def learned_leg(dev):
+    """The learned-preconditioner workload (16^4, links exp(i 0.5 H), kappa
+    0.134, csw 1): pairs from 24 training fields (4096, 20-iteration CG),
+    training of the 1-12-12-1 BF16 network (10 epochs, batch 16, Adam lr
+    1e-3), then on 8 held-out fields FGCR(20) with the trained network, the
+    untrained one, the identity and SAP against even-odd CG (FP32 and
+    FP16-spinor inner), each to true residual 1e-10."""
+    from paper_1103_1363_gb300 import learned
+    out = learned.run_experiment(device=dev, log=lambda *a: None)
+    return {"workload": "16^4, 24 training + 8 held-out fields, exp(i 0.5 H), kappa 0.134, csw 1.0, "
+                        "net 1-12-12-1 BF16, FGCR(20), tol 1e-10",
+            "pairs_s": round(out["pairs_s"], 2), "train_s": round(out["train_s"], 2),
+            "loss_first_last": [out["loss_history"][0], out["loss_history"][-1]],
+            "solvers": {k: {"iterations_mean": v["iterations_mean"], "ms_mean": round(1e3 * v["wall_s_mean"], 2),
+                            "true_residual_max": v["true_residual_max"], "all_converged": v["all_converged"]}
+                        for k, v in out["summary"].items()}}
 
 
 def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
@@ -573,6 +704,49 @@ def oracle_sample(w, napply):
             "cores": oracle.num_threads()}
 
 
+def oracle_solves():
+    """The oracle's full solves on the host cores: 4^4 Haar (kappa 0.12, no
+    clover) by CG on M^dag M and 16^3x32 (exp(i 0.5 H) links, kappa 0.135,
+    csw 1) by even-odd CG, both to true residual 1e-10, on all cores and on
+    one core; the one-core 16^3x32 solve runs 10 iterations and is
+    extrapolated to the all-core run's iteration count (labelled)."""
+    import oracle
+    import synth
+    cores = oracle.num_threads()
+    out = {"cores_all": cores}
+    d0 = (4, 4, 4, 4)
+    U0, b0 = synth.haar_gauge(d0, 1), synth.gaussian_spinor(d0, 0)
+    d1 = (16, 16, 16, 32)
+    U1, b1 = synth.smooth_gauge(d1, 0.5, 2), synth.gaussian_spinor(d1, 0)
+    t0 = time.perf_counter()
+    A1 = oracle.clover(U1, 0.135, 1.0)
+    A1inv, _ = oracle.invert_site_matrices(A1)
+    out["c1_clover_setup_s"] = round(time.perf_counter() - t0, 3)
+    try:
+        for label, n in (("all_cores", cores), ("one_core", 1)):
+            oracle.set_num_threads(n)
+            t0 = time.perf_counter()
+            _, it, res, ok = oracle.cgnr(U0, None, 0.12, b0)
+            out["c0_4c4_cgnr_" + label] = {"seconds": round(time.perf_counter() - t0, 4), "iterations": it,
+                                           "true_residual": res, "converged": ok, "threads": n}
+        oracle.set_num_threads(cores)
+        t0 = time.perf_counter()
+        _, it, res, ok = oracle.eo_cg(U1, A1, A1inv, 0.135, b1)
+        t_all = time.perf_counter() - t0
+        out["c1_16c32_eo_cg_all_cores"] = {"seconds": round(t_all, 3), "iterations": it, "true_residual": res,
+                                           "converged": ok, "threads": cores}
+        oracle.set_num_threads(1)
+        t0 = time.perf_counter()
+        oracle.schur_cg_iters(U1, A1, A1inv, 0.135, b1, 10)
+        t10 = time.perf_counter() - t0
+        out["c1_16c32_eo_cg_one_core"] = {"seconds_per_iteration": round(t10 / 10, 4),
+                                          "seconds_extrapolated": round(t10 / 10 * it, 2),
+                                          "note": "10 iterations timed, extrapolated to %d" % it, "threads": 1}
+    finally:
+        oracle.set_num_threads(cores)
+    return out
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -621,6 +795,7 @@ def main():
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18], help="link storage of --kernel hop")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch of --kernel hop")
     ap.add_argument("--cpu-applications", type=int, default=3)
+    ap.add_argument("--skip-learned", action="store_true", help="leave out the learned-preconditioner leg")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -646,7 +821,8 @@ def main():
             cpu = {"value": o["gflops"], "unit": "GFLOP/s", "cores": o["cores"], "kind": "oracle",
                    "sample": "%d applications of the oracle's even-odd Schur operator (2 hopping terms "
                              "each) on the full %s lattice, FP64, OpenMP on all host cores"
-                             % (args.cpu_applications, "x".join(map(str, w["dims"])))}
+                             % (args.cpu_applications, "x".join(map(str, w["dims"]))),
+                   "solves": oracle_solves()}
         ms_step = r["ms"] / args.steps
         line = {
             "metric": METRIC, "value": round(r["value"], 2), "unit": "GFLOP/s", "n_gpus": world,
@@ -665,6 +841,7 @@ def main():
                                "true_residual_max": r["worst_res"]},
             "clover_setup_s": r["clover_setup_s"], "tuned": r["tuned"],
             "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"),
+            "multi_rhs": r.get("multi_rhs"), "learned": r.get("learned"),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -43,6 +43,7 @@ _PREC = C.CFUNCTYPE(None, _P, _P, _P)
 
 _SIGS = {
     "oracle_num_threads": (_I, []),
+    "oracle_set_num_threads": (None, [_I]),
     "oracle_gamma": (None, [_I, _P]),
     "oracle_sigma": (None, [_I, _I, _P]),
     "oracle_hop": (None, [_P, _I, _P, _P, _P]),
@@ -99,6 +100,11 @@ def use_library(path):
 def num_threads():
     """Threads of the oracle's OpenMP loops (the cores a timed run uses)."""
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n):
+    """Run later OpenMP loops of the oracle on n threads (timing only)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def _c(a):

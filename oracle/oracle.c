@@ -910,3 +910,14 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of later OpenMP loops (timing on a given number of cores; no
+ * effect on any result beyond the summation order of the reductions). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -62,11 +62,12 @@ def make_pairs(lat, npairs, seed, cg_iters=20, with_start=True, chunk=None):
     R = torch.empty((npairs,) + shape, dtype=torch.complex64, device=lat.device)
     E = torch.empty_like(R)
     runs = npairs // 2 if with_start else npairs
-    gen = torch.Generator(device="cpu").manual_seed(int(seed))
+    # x* drawn on the device (seeded): complex Gaussian, E|z|^2 = 1 per component
+    gen = torch.Generator(device=lat.device).manual_seed(int(seed))
     k = 0
     for p0 in range(0, runs, chunk):
         n = min(chunk, runs - p0)
-        xs = (torch.randn((n,) + shape, dtype=torch.complex128, generator=gen)).to(lat.device)
+        xs = torch.randn((n,) + shape, dtype=torch.complex128, device=lat.device, generator=gen)
         b = torch.empty_like(xs)
         apply_full_operator(lat, b, xs, n)
         x20 = torch.zeros_like(xs)
