@@ -349,6 +349,7 @@ def multi_rhs_leg(dev):
                 "launches": sum(s["kernel_launches"] for s in sts)}
 
     for name, kw in (("multi_rhs_f16spinors", dict(mixed, inner_prec="f16spinors")),
+                     ("multi_rhs_f16spinors_persistent", dict(mixed, inner_prec="f16spinors", persistent=1)),
                      ("multi_rhs_f32", dict(mixed, inner_prec="f32"))):
         t, sts = timed_solves(lat, stream, [(x, b, dict(kw, nrhs=12))])
         res[name] = summary(t, sts)
@@ -372,19 +373,20 @@ def multi_rhs_leg(dev):
         lats.append(l)
         bs.append(torch.from_numpy(synth.gaussian_spinor(d, seed + 100)).to(dev))
         xs.append(torch.zeros_like(bs[-1]))
-    p = lqcd.solver_params(inner_prec="f32", use_graph=1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ub = {"lattices": ["%dx%dx%dx%d kappa %.4g" % (d + (k,)) for d, k, _ in specs]}
-    for rep in range(2):  # warm-up, timed
-        stream.synchronize()
-        e0.record(stream)
-        rc, st = lqcd.lqcd_solve_batch([l.ctx for l in lats], xs, bs, [TOL] * 3, p, raise_on_error=False)
-        e1.record(stream)
-        stream.synchronize()
-    ub["batch_one_graph"] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "status": rc,
-                             "iterations": [s["iterations"] for s in st],
-                             "true_residual": [s["true_residual"] for s in st],
-                             "launches": sum(s["kernel_launches"] for s in st)}
+    ub = {"lattices": ["%dx%dx%dx%d kappa %.4g" % (d + (k,)) for d, k, _ in specs], "inner": "f32"}
+    for name, p in (("batch_one_graph", lqcd.solver_params(inner_prec="f32", use_graph=1)),
+                    ("batch_persistent", lqcd.solver_params(inner_prec="f32", persistent=1))):
+        for rep in range(2):  # warm-up, timed
+            stream.synchronize()
+            e0.record(stream)
+            rc, st = lqcd.lqcd_solve_batch([l.ctx for l in lats], xs, bs, [TOL] * 3, p, raise_on_error=False)
+            e1.record(stream)
+            stream.synchronize()
+        ub[name] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 4), "status": rc,
+                    "iterations": [s["iterations"] for s in st],
+                    "true_residual": [s["true_residual"] for s in st],
+                    "launches": sum(s["kernel_launches"] for s in st)}
     seq = []
     for rep in range(2):
         stream.synchronize()
@@ -453,25 +455,27 @@ def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
 
 def run_hop_kernel(args, w):
     """Stand-alone parity hopping term (recon-12) of one precision, for kernel
-    profiles: warmup + steps launches over 8 rotating buffer pairs, each
-    holding --nrhs right-hand sides (one launch serves all of them; the
-    compulsory bytes count the links once per launch)."""
+    profiles: warmup + steps launches over rotating buffer pairs, each holding
+    --nrhs right-hand sides (one launch serves all of them; the compulsory
+    bytes count the links once per launch)."""
     import torch
 
     import synth
     from paper_1103_1363_gb300 import lqcd
     dims = w["dims"]
     Vh = int(np.prod(dims)) // 2
+    R = args.nrhs  # the hopping term takes any nrhs; the context's solver vectors are not used
     stream = torch.cuda.Stream()
-    lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, stream=stream)
-    lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
+    U = torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda()
     b = synth.gaussian_spinor(dims, w["src_seed"])
-    R = args.nrhs
-    if R > 1:
-        lat.close()
-        lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, max_nrhs=R, stream=stream)
-        lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, w["eps"], w["gauge_seed"])).cuda())
     nbuf = 8 if R == 1 else 3
+    spinor = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52, "f16links": 96, "bf16links": 96, "f16spinors": 52,
+              "bf16spinors": 52}
+    link = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24, "f16links": 24, "bf16links": 24, "f16spinors": 48,
+            "bf16spinors": 48}
+    hb, src = measured_peaks()
+    lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, stream=stream)
+    lat.gauge_load(U)
     with torch.cuda.stream(stream):
         fins = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
         fouts = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
@@ -488,19 +492,53 @@ def run_hop_kernel(args, w):
     e1.record(stream)
     stream.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / args.steps
-    spinor = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52, "f16links": 96, "bf16links": 96, "f16spinors": 52,
-              "bf16spinors": 52}
-    link = {"f64": 144, "f32": 48, "f16": 24, "bf16": 24, "f16links": 24, "bf16links": 24, "f16spinors": 48,
-            "bf16spinors": 48}
     sb = spinor[args.prec]
     lb = link[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
     comp = (2 * sb * R + 8 * lb) * Vh
-    hb, src = measured_peaks()
-    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "nrhs": R, "workload": workload_name(w),
+    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "nrhs": R,
+                      "workload": workload_name(w),
                       "us_per_launch": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / R, 2),
                       "gflops": round(1320.0 * Vh * R / t / 1e9, 1),
                       "compulsory_bytes": comp, "achieved_gbs": round(comp / t / 1e9, 1),
                       "frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": src}), flush=True)
+    lat.close()
+    return 0
+
+
+def run_persist_kernel(args, w):
+    """Even-odd CG (FP32 inner, FP64 reliable updates) solved alone on 4^4,
+    8^4, 12^4, 16^3x32 and 24^3x48 lattices (links exp(i 0.5 H), kappa 0.13,
+    csw 1, Gaussian source): graph-replayed launch per stage against one
+    persistent launch per iteration block; microseconds per iteration."""
+    import torch
+
+    import synth
+    from paper_1103_1363_gb300 import lqcd
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for dims in ((4, 4, 4, 4), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)):
+        lat = lqcd.Lattice(dims, precisions=("f64", "f32"), stream=stream)
+        lat.gauge_load(torch.from_numpy(synth.smooth_gauge(dims, 0.5, 4)).cuda())
+        lat.clover_compute(0.13, 1.0)
+        b = torch.from_numpy(synth.gaussian_spinor(dims, 5)).cuda()
+        x = torch.zeros_like(b)
+        row = {"dims": list(dims)}
+        for name, kw in (("graph", dict(use_graph=1)), ("persistent", dict(persistent=1))):
+            best = None
+            for rep in range(args.warmup + args.steps):
+                stream.synchronize()
+                e0.record(stream)
+                rc, st = lat.solve(x, b, TOL, raise_on_error=False, inner_prec="f32", **kw)
+                e1.record(stream)
+                stream.synchronize()
+                t = e0.elapsed_time(e1) * 1e-3
+                if rep >= args.warmup and (best is None or t < best):
+                    best = t
+            row[name] = {"seconds": round(best, 5), "iterations": st["iterations"], "status": rc,
+                         "us_per_iteration": round(1e6 * best / max(1, st["iterations"]), 2),
+                         "true_residual": st["true_residual"], "launches": st["kernel_launches"]}
+        print(json.dumps(row), flush=True)
+        lat.close()
     return 0
 
 
@@ -782,7 +820,7 @@ def main():
     ap.add_argument("--inner", default="f16spinors", choices=["f32", "f16", "bf16", "f16links", "bf16links", "f16spinors",
                                                       "bf16spinors"],
                     help="storage of the timed solve's inner iteration")
-    ap.add_argument("--kernel", default=None, choices=["hop", "sap", "net"],
+    ap.add_argument("--kernel", default=None, choices=["hop", "sap", "net", "persist"],
                     help="instead of the solve: time the stand-alone parity hopping kernel, the SAP "
                          "preconditioner and SAP-FGCR, or the learned preconditioner's network kernels "
                          "(profiling)")
@@ -806,6 +844,8 @@ def main():
         return run_sap_kernel(args, w)
     if args.kernel == "net":
         return run_net_kernel(args, w)
+    if args.kernel == "persist":
+        return run_persist_kernel(args, w)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

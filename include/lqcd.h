@@ -189,6 +189,20 @@ typedef struct {
                                 native FP64 */
     int ndefl;               /* FGMRES-DR: harmonic Ritz vectors kept at a restart
                                 (0 <= ndefl <= 16, < nkrylov; 0: plain restarted FGMRES) */
+    int persistent;          /* 1: even-odd CG runs each block of check_interval inner
+                                iterations as one persistent cooperative launch over
+                                every lattice and right-hand side of the call (grid
+                                barriers between the four hopping stages, the two
+                                reductions and the direction update); for small
+                                lattices, whose launches are latency-bound.  Needs
+                                LQCD_SOLVER_CG_EO, inner_prec LQCD_F32, LQCD_F16_SPINORS
+                                or LQCD_BF16_SPINORS, at most 8 lattices and 64
+                                right-hand sides in all; use_graph is then ignored.
+                                The iterates agree with the launch-per-stage path up
+                                to the summation order of the global sums. */
+    int persistent_wait_us;  /* bound of each grid-barrier wait of the persistent launch
+                                (0: 2 s); a wait that expires ends the launch and the
+                                solve returns LQCD_ERR_TIMEOUT */
 } lqcd_solver_params;
 
 typedef struct {
@@ -208,7 +222,7 @@ typedef struct {
 } lqcd_solver_stats;
 
 /* Defaults: CG_EO, F32 inner, maxiter 100000, reliable every 50, delta 0.1,
- * check every 10, nkrylov 20, no graph, ndefl 0.
+ * check every 10, nkrylov 20, no graph, ndefl 0, not persistent.
  *
  * LQCD_SOLVER_FGCR and LQCD_SOLVER_FGMRES_DR run their recursion on FP32
  * full fields (inner_prec F32, F16_LINKS or BF16_LINKS for the operator) and
@@ -404,9 +418,10 @@ lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[4], int best
  * recorded).  lqcd_profile_read waits for the stream and returns, for each
  * storage precision (index lqcd_prec), the launches since the last read,
  * their summed device time, and their algorithmic bytes and flops: bytes
- * count every input field, link, clover entry and output of the launch
- * once per output site (the compulsory traffic), flops count 1320 per
- * output site and right-hand side (the hopping term alone). */
+ * count every right-hand side's input and epilogue fields and output once
+ * per output site, and the links and clover entry once per output site and
+ * launch (the compulsory traffic), flops count 1320 per output site and
+ * right-hand side (the hopping term alone). */
 typedef struct {
     long launches;
     double ms;

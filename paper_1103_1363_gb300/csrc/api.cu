@@ -80,23 +80,24 @@ struct Profiler {
     }
 };
 
-// Compulsory bytes of one launch per output site and right-hand side:
-// input spinor, 8 links, and each epilogue operand once.
-static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int mode, int epi)
+// Compulsory bytes of one launch per output site: every right-hand side's
+// input spinor and epilogue vectors, and the 8 links and the clover entry
+// once (shared by all right-hand sides).
+static double launch_bytes_per_site(const lqcd_ctx* c, const DslashArgs& A, int mode, int epi, int nrhs)
 {
     const int pg = mode_pg(mode), ps = mode_ps(mode);
     const double S = (double)spinor_field_bytes(ps, 1);
     const double L = (double)gauge_link_bytes(pg, c->recon_of(pg));
     const double Cl = A.clov ? (double)clover_site_bytes(pg) : 0.0;
     const double Acc = (double)spinor_field_bytes(AccumPrec(ps), 1);
-    double b = S + 8 * L;
+    double per_rhs = S;
     switch (epi) {
-    case EPI_NONE: b += S; break;
-    case EPI_CLOVINV: b += S + Cl; break;
-    case EPI_XPAY: b += 2 * S + Cl; break;
-    default: b += 2 * S + Cl + 4 * Acc; break;  // y, p read; x, r read and written
+    case EPI_NONE: per_rhs += S; break;
+    case EPI_CLOVINV: per_rhs += S; break;
+    case EPI_XPAY: per_rhs += 2 * S; break;
+    default: per_rhs += 2 * S + 4 * Acc; break;  // y, p read; x, r read and written
     }
-    return b;
+    return nrhs * per_rhs + 8 * L + (epi == EPI_NONE ? 0.0 : Cl);
 }
 
 lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A0, int P, bool dag, int epi, bool red, int nrhs)
@@ -133,9 +134,8 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A0, int P, bool dag, in
     LQ_CUDA(e);
     if (timed) {
         LQ_CUDA(cudaEventRecord(rec.b, c->stream));
-        const double sites = (double)c->g.Vh * nrhs;
-        rec.bytes = launch_bytes_per_site(c, A, P, epi) * sites;
-        rec.flops = 1320.0 * sites;
+        rec.bytes = launch_bytes_per_site(c, A, P, epi, nrhs) * c->g.Vh;
+        rec.flops = 1320.0 * c->g.Vh * nrhs;
         pr->pending.push_back(rec);
     }
     c->dslash_count += nrhs;
@@ -307,6 +307,7 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     c->gcr_bytes = cfg->gcr_nkrylov > 0 ? (size_t)(2 * cfg->gcr_nkrylov + 3) * 2 * c->field_bytes(P32) + GCR_SCALAR_BYTES
                                         : 0;
     take(c->s_gcr, c->gcr_bytes);
+    take(c->s_persist, PERSIST_SCRATCH_BYTES);
     c->need = off;
     *out = c;
     return LQCD_OK;
@@ -396,6 +397,7 @@ lqcd_status lqcd_set_workspace(lqcd_ctx* c, void* ptr, size_t bytes)
     c->veclo = at(c->s_veclo);
     c->vecacc = at(c->s_vecacc);
     c->gcr = at(c->s_gcr);
+    c->persist = at(c->s_persist);
     LQ_CUDA(cudaMemsetAsync(c->tickets, 0, c->s_tickets.bytes, c->stream));
     LQ_CUDA(cudaMemsetAsync(c->errw, 0, c->s_errw.bytes, c->stream));
     LQ_CUDA(cudaMemsetAsync(c->skip, 0, c->s_skip.bytes, c->stream));
@@ -750,6 +752,8 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
     p->nkrylov = 20;
     p->use_graph = 0;
     p->ndefl = 0;
+    p->persistent = 0;
+    p->persistent_wait_us = 0;
     // native FP64: the double-float kernels measured slower on GB300 (255
     // registers, one 4-warp block per SM, dependent FP32 chains)
     p->residual_prec = LQCD_F64;

@@ -281,8 +281,15 @@ __device__ __forceinline__ void reconstruct_row2(R u[18])
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         const int c = (b + 1) % 3, d = (b + 2) % 3;
-        R re = RE(0, c) * RE(1, d) - IM(0, c) * IM(1, d) - (RE(0, d) * RE(1, c) - IM(0, d) * IM(1, c));
-        R im = RE(0, c) * IM(1, d) + IM(0, c) * RE(1, d) - (RE(0, d) * IM(1, c) + IM(0, d) * RE(1, c));
+        // u0c u1d - u0d u1c, one multiply-add per real product
+        R re = RE(0, c) * RE(1, d);
+        re -= IM(0, c) * IM(1, d);
+        re -= RE(0, d) * RE(1, c);
+        re += IM(0, d) * IM(1, c);
+        R im = RE(0, c) * IM(1, d);
+        im += IM(0, c) * RE(1, d);
+        im -= RE(0, d) * IM(1, c);
+        im -= IM(0, d) * RE(1, c);
         RE(2, b) = re;
         IM(2, b) = -im;
     }
@@ -541,10 +548,15 @@ __device__ __forceinline__ void hermitian6_apply(const R c[36], const R v[12], R
         for (int s = 0; s < r; ++s) {
             const R lr = c[k], li = c[k + 1];  // L[r][s]; C[s][r] = conj(L[r][s])
             k += 2;
-            out[2 * r] += lr * v[2 * s] - li * v[2 * s + 1];
-            out[2 * r + 1] += lr * v[2 * s + 1] + li * v[2 * s];
-            out[2 * s] += lr * v[2 * r] + li * v[2 * r + 1];
-            out[2 * s + 1] += lr * v[2 * r + 1] - li * v[2 * r];
+            // one multiply-add per real product
+            out[2 * r] += lr * v[2 * s];
+            out[2 * r] -= li * v[2 * s + 1];
+            out[2 * r + 1] += lr * v[2 * s + 1];
+            out[2 * r + 1] += li * v[2 * s];
+            out[2 * s] += lr * v[2 * r];
+            out[2 * s] += li * v[2 * r + 1];
+            out[2 * s + 1] += lr * v[2 * r + 1];
+            out[2 * s + 1] -= li * v[2 * r];
         }
     }
 }

@@ -117,7 +117,9 @@ __device__ __forceinline__ void accumulate(R acc[24], const R w[12])
     }
 }
 
-// w = U h (ADJ = false) or U^dag h (ADJ = true) for both colour vectors of h
+// w = U h (ADJ = false) or U^dag h (ADJ = true) for both colour vectors of h.
+// Each real product is its own multiply-add into the running sum (one
+// fused instruction each; a - b*c contracts with the sign folded in).
 template <bool ADJ, class R>
 __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[12])
 {
@@ -125,14 +127,26 @@ __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[1
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            R re = 0, im = 0;
+            R re, im;
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const int k = ADJ ? 2 * (3 * b + a) : 2 * (3 * a + b);
-                const R ur = u[k], ui = ADJ ? -u[k + 1] : u[k + 1];
+                const R ur = u[k], ui = u[k + 1];
                 const R hr = h[2 * (3 * s + b)], hi = h[2 * (3 * s + b) + 1];
-                re += ur * hr - ui * hi;
-                im += ur * hi + ui * hr;
+                if (b == 0) {
+                    re = ur * hr;
+                    im = ur * hi;
+                } else {
+                    re += ur * hr;
+                    im += ur * hi;
+                }
+                if (ADJ) {  // conj(u): (ur - i ui)(hr + i hi)
+                    re += ui * hi;
+                    im -= ui * hr;
+                } else {
+                    re -= ui * hi;
+                    im += ui * hr;
+                }
             }
             w[2 * (3 * s + a)] = re;
             w[2 * (3 * s + a) + 1] = im;
@@ -289,27 +303,13 @@ __device__ __forceinline__ void hop_all_half(const DslashArgs& A, const char* in
 #define LQCD_DSLASH_MINB 4  // <= 128 registers; 4, 5, 6 measured within 5% on 32^3x64
 #endif
 #define DSLASH_MAX_BLOCK 128
-// The hopping term and epilogue at output site i of right-hand side rhs;
-// nrm accumulates |out|^2 (|r|^2 for EPI_CG).
-template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
-__device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i, double& nrm)
+// Epilogue at output site i of right-hand side rhs for the hopping term
+// acc; nrm accumulates |out|^2 (|r|^2 for EPI_CG).
+template <int PG, int PS, bool DAG, int EPI, bool RED>
+__device__ __forceinline__ void dslash_epilogue(const DslashArgs& A, int rhs, int i, typename RealT<PS>::type acc[24],
+                                                double& nrm)
 {
     typedef typename RealT<PS>::type R;
-    int c[4];
-    cb_coords(A.g, i, A.par, c);
-    const int full = full_index(A.g, c);
-    const char* in = static_cast<const char*>(A.in) + rhs * A.in_rb;
-    R acc[24];
-#pragma unroll
-    for (int k = 0; k < 24; ++k) acc[k] = 0;
-    if constexpr ((PS == P16 || PS == PB16) && PG == PS) {
-        hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG>(A, in, i, full, c, acc);
-    } else {
-        hop_dir<PG, PS, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
-        hop_dir<PG, PS, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
-        hop_dir<PG, PS, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
-        hop_dir<PG, PS, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
-    }
     const R a = (R)A.a;
     if (EPI == EPI_NONE) {
 #pragma unroll
@@ -371,9 +371,36 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i,
     }
 }
 
+// The hopping term and epilogue at output site i of right-hand side rhs;
+// nrm accumulates |out|^2 (|r|^2 for EPI_CG).
+template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
+__device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i, double& nrm)
+{
+    typedef typename RealT<PS>::type R;
+    int c[4];
+    cb_coords(A.g, i, A.par, c);
+    const int full = full_index(A.g, c);
+    const char* in = static_cast<const char*>(A.in) + rhs * A.in_rb;
+    R acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+    if constexpr ((PS == P16 || PS == PB16) && PG == PS) {
+        hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG>(A, in, i, full, c, acc);
+    } else {
+        hop_dir<PG, PS, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
+        hop_dir<PG, PS, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
+        hop_dir<PG, PS, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
+        hop_dir<PG, PS, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+    }
+    dslash_epilogue<PG, PS, DAG, EPI, RED>(A, rhs, i, acc, nrm);
+}
+
 // One-dimensional grid: block b serves right-hand side b % nrhs and site
 // block b / nrhs, so that the blocks of all right-hand sides for the same
 // sites run together and share each link (and clover) read through L2.
+// (Applying each loaded link to several right-hand sides in one thread was
+// measured slower: the extra accumulators cost occupancy in a kernel whose
+// neighbour gathers are latency-bound.)
 template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
 __global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 1 : LQCD_DSLASH_MINB))
     dslash_kernel(const DslashArgs A)

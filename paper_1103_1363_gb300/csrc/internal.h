@@ -83,6 +83,60 @@ cudaError_t dslash_dispatch_bf16spinors(const DslashArgs&, int, bool, int, bool,
 
 struct Profiler;  // api.cu: CUDA-event timing of hopping-term launches
 
+// ---- persistent even-odd CG (persistent.cu)
+// Work of a stage: every (lattice, rhs) pair is cut into tiles of
+// PERSIST_THREADS x spt sites (spt sites per thread, so that a pair has at
+// most PERSIST_MAX_TILES tiles); the tiles of all pairs are spread over the
+// grid in one pass.
+enum { PERSIST_THREADS = 128, PERSIST_MAXL = 8, PERSIST_MAXPAIRS = 64, PERSIST_MAX_TILES = 1024,
+       PERSIST_MAX_GRID = 2048 };
+// workspace bytes of the persistent launch's reduction partials (one per
+// tile), tickets, barrier words and abort word (in the first context of a solve)
+enum : size_t {
+    PERSIST_SCRATCH_BYTES = (size_t)PERSIST_MAXPAIRS * PERSIST_MAX_TILES * sizeof(double) + 4096
+};
+
+// One lattice's part of a persistent iteration block.  Inside the block
+// the |r|^2 slots form a ring of two (iteration j reads slot j mod 2 and
+// writes (j + 1) mod 2) and |Mhat p|^2 uses one slot, so the stage
+// arguments of even and odd iterations are fixed and set by the host.
+struct PersistLattice {
+    DslashArgs d[2][4];    // [j mod 2][stage]: the four hopping stages of an iteration
+    Geom g;
+    int R;                 // right-hand sides
+    int pair0;             // index of the lattice's first (lattice, rhs) reduction slot
+    int spt;               // sites per thread of the lattice's tiles
+    int ntiles;            // tiles per right-hand side
+    char* p;               // p_o (inner storage), rhs stride p_rb
+    size_t p_rb;
+    const char* r;         // r_o (FP32 accumulation), rhs stride r_rb
+    size_t r_rb;
+    double* scal;          // per-rhs scalar slots (stride SC_PER_RHS)
+    const int* skip;       // per-rhs converged flags
+};
+
+struct PersistArgs {
+    int nlat;
+    int npairs;
+    int tile0[PERSIST_MAXPAIRS + 1];        // first tile of each pair; tile0[npairs] = all tiles
+    unsigned char pair_lat[PERSIST_MAXPAIRS];
+    unsigned char pair_rhs[PERSIST_MAXPAIRS];
+    int niter;             // iterations of the block
+    int last_p;            // 1: the block's last iteration also updates p (no reliable update follows)
+    int copy_slots;        // 1: at the end, |r|^2 slot 0 <- slot niter
+    double* partials;      // [pair][gridDim.x]
+    unsigned* tickets;     // [pair]
+    unsigned* bar;         // [0] arrivals, [1] generation
+    int* abort;            // raised by a block whose barrier wait expired
+    int* errw;             // error word of the first context
+    unsigned long long wait_ns;
+    PersistLattice lat[PERSIST_MAXL];
+};
+bool persist_supported(int mode);
+// blocks of the persistent launch for ntiles tiles in all
+lqcd_status persist_grid(int mode, int recon, int ntiles, int* grid);
+lqcd_status launch_persist(lqcd_ctx* c0, const PersistArgs& P, int mode, int recon, int grid);
+
 }  // namespace lqcd
 
 struct lqcd_ctx {
@@ -102,7 +156,7 @@ struct lqcd_ctx {
     size_t need;
     struct Slot { size_t off, bytes; };
     Slot s_gauge[4], s_clov[4], s_clovinv[4];
-    Slot s_staging, s_partials, s_tickets, s_scal, s_errw, s_skip, s_vec64, s_veclo, s_vecacc, s_gcr;
+    Slot s_staging, s_partials, s_tickets, s_scal, s_errw, s_skip, s_vec64, s_veclo, s_vecacc, s_gcr, s_persist;
     void* gauge[4];          // per precision copy, layout [parity][mu][chunk][stride]
     void* clov[4];           // A, layout [parity][chunk][stride] (parity stride clov_pb[p])
     void* clovinv[4];
@@ -119,6 +173,7 @@ struct lqcd_ctx {
     char* vecacc;            // accumulation vectors (x_lo, r): FP64-sized
     char* gcr;               // FGCR Krylov vectors
     size_t gcr_bytes;
+    char* persist;           // persistent CG launch: reduction partials, tickets, barrier and abort words
 
     // state
     int gauge_loaded;

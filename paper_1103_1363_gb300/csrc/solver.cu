@@ -27,8 +27,6 @@
 
 namespace lqcd {
 
-namespace {
-
 struct Cg {
     lqcd_ctx* c;
     int R;          // right-hand sides
@@ -44,13 +42,74 @@ struct Cg {
     long reliable = 0, checks = 0;
 };
 
-const void* clov_or_null(lqcd_ctx* c, int P, int parity, bool inverse)
+static const void* clov_or_null(lqcd_ctx* c, int P, int parity, bool inverse)
 {
     if (c->csw == 0.0) return nullptr;
     const int pg = mode_pg(P);
     const char* base = static_cast<const char*>(inverse ? c->clovinv[pg] : c->clov[pg]);
     return base + parity * c->clov_parity_bytes(pg);
 }
+
+// The four hopping launches of an even-odd CG iteration j (block-relative
+// scalar slots):
+//   D1: t_e = A_ee^{-1} H_eo p_o
+//   D2: q_o = A_oo p_o - kappa^2 H_oe t_e,               |q_o|^2 -> pap slot j
+//   D3: t_e = A_ee^{-1} H_eo^dag q_o
+//   D4: s = A_oo q_o - kappa^2 H_oe^dag t_e; x += alpha p; r -= alpha s,
+//       alpha = |r|^2 / |q|^2 from slots j,                |r|^2 -> rr slot j + 1
+// (D1, D3: EPI_CLOVINV; D2: EPI_XPAY with the norm; D4: EPI_CG, dagger for D3, D4.)
+void eo_stage_args(const Cg& s, int j, DslashArgs d[4])
+{
+    lqcd_ctx* c = s.c;
+    const int P = s.Pi;
+    DslashArgs A = base_args(c, P);
+    A.skip = c->skip;
+    A.par = 0;
+    A.out = s.Qv;
+    A.out_rb = s.rbi;
+    A.in = s.Pv + s.fbi;
+    A.in_rb = s.rbi;
+    A.clov = clov_or_null(c, P, 0, true);
+    A.a = 1.0;
+    d[0] = A;
+    DslashArgs B = base_args(c, P);
+    B.skip = c->skip;
+    B.par = 1;
+    B.out = s.Qv + s.fbi;
+    B.out_rb = s.rbi;
+    B.in = s.Qv;
+    B.in_rb = s.rbi;
+    B.clov = clov_or_null(c, P, 1, false);
+    B.y = s.Pv + s.fbi;
+    B.y_rb = s.rbi;
+    B.a = -c->kappa * c->kappa;
+    B.red = c->scal + pap_slot(j) + 1;
+    d[1] = B;
+    A.in = s.Qv + s.fbi;
+    d[2] = A;
+    DslashArgs D = base_args(c, P);
+    D.skip = c->skip;
+    D.par = 1;
+    D.in = s.Qv;
+    D.in_rb = s.rbi;
+    D.clov = clov_or_null(c, P, 1, false);
+    D.y = s.Qv + s.fbi;
+    D.y_rb = s.rbi;
+    D.a = -c->kappa * c->kappa;
+    D.x = s.XLO + s.fba;
+    D.r = s.RV + s.fba;
+    D.acc_rb = s.rba;
+    D.p = s.Pv + s.fbi;
+    D.p_rb = s.rbi;
+    D.s_num = rr_slot(j);
+    D.s_num2 = rr_slot(j) + 1;
+    D.s_den = pap_slot(j);
+    D.s_den2 = pap_slot(j) + 1;
+    D.red = c->scal + rr_slot(j + 1) + 1;
+    d[3] = D;
+}
+
+namespace {
 
 // One inner CG iteration j of a block: q = K p, x += alpha p, r -= alpha K^dag q
 // with K = Mhat (eo) or M (full), |r|^2 into block slot j + 1.
@@ -59,55 +118,12 @@ lqcd_status cg_iteration(Cg& s, int j)
     lqcd_ctx* c = s.c;
     const int P = s.Pi;
     if (s.eo) {
-        // D1: t_e = A_ee^{-1} H_eo p_o
-        DslashArgs A = base_args(c, P);
-        A.skip = c->skip;
-        A.par = 0;
-        A.out = s.Qv;
-        A.out_rb = s.rbi;
-        A.in = s.Pv + s.fbi;
-        A.in_rb = s.rbi;
-        A.clov = clov_or_null(c, P, 0, true);
-        A.a = 1.0;
-        LQ_TRY(launch_dslash(c, A, P, false, EPI_CLOVINV, false, s.R));
-        // D2: q_o = A_oo p_o - kappa^2 H_oe t_e, |q|^2 -> pap slot j
-        DslashArgs B = base_args(c, P);
-        B.skip = c->skip;
-        B.par = 1;
-        B.out = s.Qv + s.fbi;
-        B.out_rb = s.rbi;
-        B.in = s.Qv;
-        B.in_rb = s.rbi;
-        B.clov = clov_or_null(c, P, 1, false);
-        B.y = s.Pv + s.fbi;
-        B.y_rb = s.rbi;
-        B.a = -c->kappa * c->kappa;
-        B.red = c->scal + pap_slot(j) + 1;
-        LQ_TRY(launch_dslash(c, B, P, false, EPI_XPAY, true, s.R));
-        // D3: t_e = A_ee^{-1} H_eo^dag q_o
-        A.in = s.Qv + s.fbi;
-        LQ_TRY(launch_dslash(c, A, P, true, EPI_CLOVINV, false, s.R));
-        // D4: s = A_oo q_o - kappa^2 H_oe^dag t_e; x += alpha p; r -= alpha s
-        DslashArgs D = base_args(c, P);
-        D.skip = c->skip;
-        D.par = 1;
-        D.in = s.Qv;
-        D.in_rb = s.rbi;
-        D.clov = clov_or_null(c, P, 1, false);
-        D.y = s.Qv + s.fbi;
-        D.y_rb = s.rbi;
-        D.a = -c->kappa * c->kappa;
-        D.x = s.XLO + s.fba;
-        D.r = s.RV + s.fba;
-        D.acc_rb = s.rba;
-        D.p = s.Pv + s.fbi;
-        D.p_rb = s.rbi;
-        D.s_num = rr_slot(j);
-        D.s_num2 = rr_slot(j) + 1;
-        D.s_den = pap_slot(j);
-        D.s_den2 = pap_slot(j) + 1;
-        D.red = c->scal + rr_slot(j + 1) + 1;
-        LQ_TRY(launch_dslash(c, D, P, true, EPI_CG, true, s.R));
+        DslashArgs d[4];
+        eo_stage_args(s, j, d);
+        LQ_TRY(launch_dslash(c, d[0], P, false, EPI_CLOVINV, false, s.R));
+        LQ_TRY(launch_dslash(c, d[1], P, false, EPI_XPAY, true, s.R));
+        LQ_TRY(launch_dslash(c, d[2], P, true, EPI_CLOVINV, false, s.R));
+        LQ_TRY(launch_dslash(c, d[3], P, true, EPI_CG, true, s.R));
     } else {
         // q = M p on both parities, |q|^2 per parity -> pap slot j (+0, +1)
         for (int par = 0; par < 2; ++par) {
@@ -529,6 +545,119 @@ lqcd_status cg_finish(CgRun& run, lqcd_solver_stats* st)
     return LQCD_OK;
 }
 
+// One block of n iterations of every active run as persistent launches (one
+// per inner precision present: a 16-bit run that fell back to FP32 forms its
+// own group); with a reliable update at its end a launch stops before the
+// last direction update, and the update, the direction update and the slot
+// copy follow as separate launches (as in run_block).  Inside the launch the
+// |r|^2 slots are a ring of two: the block's final |r|^2 is in slot n mod 2.
+lqcd_status run_block_persistent(std::vector<CgRun*>& runs, unsigned long long mask, int n, bool ru,
+                                 const lqcd_solver_params* p)
+{
+    lqcd_ctx* c0 = runs[0]->c;
+    char* w = c0->persist;
+    double* partials = reinterpret_cast<double*>(w);
+    unsigned* tickets = reinterpret_cast<unsigned*>(w + (size_t)PERSIST_MAXPAIRS * PERSIST_MAX_TILES * sizeof(double));
+    int* abort_word = reinterpret_cast<int*>(tickets + PERSIST_MAXPAIRS + 2);
+    unsigned long long todo = mask;
+    while (todo) {
+        int mode = -1, recon = -1, pairs = 0;
+        PersistArgs P;
+        memset(&P, 0, sizeof(P));
+        std::vector<size_t> members;
+        for (size_t i = 0; i < runs.size(); ++i) {
+            if (!(todo >> i & 1)) continue;
+            Cg& s = runs[i]->s;
+            if (!s.eo) return fail(LQCD_ERR_INVALID, "persistent CG: even-odd CG only");
+            const int rc = s.c->recon_of(mode_pg(s.Pi));
+            if (mode < 0) {
+                mode = s.Pi;
+                recon = rc;
+            }
+            if (s.Pi != mode || rc != recon) continue;  // a later group
+            if ((int)members.size() == PERSIST_MAXL) return fail(LQCD_ERR_INVALID, "persistent CG: at most 8 lattices");
+            if (pairs + s.R > PERSIST_MAXPAIRS)
+                return fail(LQCD_ERR_INVALID, "persistent CG: at most 64 right-hand sides");
+            members.push_back(i);
+            pairs += s.R;
+        }
+        pairs = 0;
+        int ntiles = 0;
+        for (size_t m : members) {
+            todo &= ~(1ull << m);
+            Cg& s = runs[m]->s;
+            lqcd_ctx* c = s.c;
+            PersistLattice& L = P.lat[P.nlat++];
+            for (int jj = 0; jj < 2; ++jj) {
+                eo_stage_args(s, jj, L.d[jj]);
+                L.d[jj][3].red = c->scal + rr_slot((jj + 1) & 1) + 1;  // the ring of two
+                for (int k = 0; k < 4; ++k) {
+                    L.d[jj][k].nrhs = s.R;
+                    L.d[jj][k].partials = partials + (size_t)pairs * PERSIST_MAX_TILES;
+                    L.d[jj][k].part_rs = PERSIST_MAX_TILES;
+                    L.d[jj][k].tickets = tickets + pairs;
+                }
+            }
+            L.g = c->g;
+            L.R = s.R;
+            L.pair0 = pairs;
+            const long per = (long)PERSIST_THREADS * PERSIST_MAX_TILES;
+            L.spt = (int)((c->g.Vh + per - 1) / per);
+            L.ntiles = (c->g.Vh + PERSIST_THREADS * L.spt - 1) / (PERSIST_THREADS * L.spt);
+            for (int r = 0; r < s.R; ++r) {
+                P.tile0[P.npairs] = ntiles;
+                P.pair_lat[P.npairs] = (unsigned char)(P.nlat - 1);
+                P.pair_rhs[P.npairs] = (unsigned char)r;
+                P.npairs++;
+                ntiles += L.ntiles;
+            }
+            L.p = s.Pv + s.fbi;
+            L.p_rb = s.rbi;
+            L.r = s.RV + s.fba;
+            L.r_rb = s.rba;
+            L.scal = c->scal;
+            L.skip = c->skip;
+            pairs += s.R;
+            c->dslash_count += 4L * n * s.R;
+            c->launches++;
+        }
+        P.tile0[P.npairs] = ntiles;
+        int grid = 0;
+        LQ_TRY(persist_grid(mode, recon, ntiles, &grid));
+        P.niter = n;
+        P.last_p = ru ? 0 : 1;
+        P.copy_slots = ru ? 0 : 1;
+        P.partials = partials;
+        P.tickets = tickets;
+        P.bar = tickets + PERSIST_MAXPAIRS;
+        P.abort = abort_word;
+        P.errw = c0->errw;
+        P.wait_ns = p->persistent_wait_us > 0 ? 1000ull * (unsigned long long)p->persistent_wait_us : 2000000000ull;
+        // tickets, barrier words and abort word start at zero (an aborted launch leaves them set)
+        LQ_CUDA(cudaMemsetAsync(tickets, 0, (PERSIST_MAXPAIRS + 3) * sizeof(unsigned), c0->stream));
+        LQ_TRY(launch_persist(c0, P, mode, recon, grid));
+        int aborted = 0;
+        LQ_CUDA(cudaMemcpyAsync(&aborted, abort_word, sizeof(int), cudaMemcpyDeviceToHost, c0->stream));
+        LQ_CUDA(cudaStreamSynchronize(c0->stream));
+        if (aborted) return fail(LQCD_ERR_TIMEOUT, "persistent CG: a grid-barrier wait expired");
+    }
+    if (ru) {
+        const int jn = n & 1, jp = (n - 1) & 1;
+        for (size_t i = 0; i < runs.size(); ++i) {
+            if (!(mask >> i & 1)) continue;
+            Cg& s = runs[i]->s;
+            LQ_TRY(reliable_update(s, jn));
+            LQ_TRY(blas_cg_p_update(s.c, s.Pv + s.oi, mode_ps(s.Pi), s.RV + s.oa, s.PA, s.R, s.rbi, s.rba, s.nf,
+                                    rr_slot(jn), rr_slot(jp)));
+            if (jn) {
+                LQ_TRY(blas_copy_scalar(s.c, rr_slot(0), rr_slot(1), s.R));
+                LQ_TRY(blas_copy_scalar(s.c, rr_slot(0) + 1, rr_slot(1) + 1, s.R));
+            }
+        }
+    }
+    return LQCD_OK;
+}
+
 void destroy_graphs(std::vector<BlockGraph>& cache)
 {
     for (auto& e : cache)
@@ -541,7 +670,8 @@ void destroy_graphs(std::vector<BlockGraph>& cache)
 lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
 {
     lqcd_ctx* c0 = runs[0]->c;
-    const bool graphs = p->use_graph && c0->stream != nullptr;
+    const bool persistent = p->persistent != 0;
+    const bool graphs = !persistent && p->use_graph && c0->stream != nullptr;
     std::vector<BlockGraph> cache;
     while (true) {
         unsigned long long mask = 0;
@@ -569,7 +699,10 @@ lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
         }
         if (ru_next) ru = true;
         for (auto* r : runs) r->ru_next = false;
-        if (graphs) {
+        if (persistent) {
+            lqcd_status ps = run_block_persistent(runs, mask, n, ru, p);
+            if (ps != LQCD_OK) return ps;
+        } else if (graphs) {
             BlockGraph* gph = nullptr;
             for (auto& e : cache)
                 if (e.n == n && e.ru == ru && e.mask == mask) gph = &e;

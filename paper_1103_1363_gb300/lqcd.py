@@ -48,7 +48,8 @@ class lqcd_solver_params(C.Structure):
     _fields_ = [("solver", C.c_int), ("inner_prec", C.c_int), ("maxiter", C.c_int),
                 ("reliable_interval", C.c_int), ("reliable_delta", C.c_double),
                 ("check_interval", C.c_int), ("nkrylov", C.c_int), ("use_graph", C.c_int),
-                ("residual_prec", C.c_int), ("ndefl", C.c_int)]
+                ("residual_prec", C.c_int), ("ndefl", C.c_int), ("persistent", C.c_int),
+                ("persistent_wait_us", C.c_int)]
 
 
 class lqcd_solver_stats(C.Structure):

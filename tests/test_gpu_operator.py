@@ -132,26 +132,39 @@ def test_wilson_without_clover(lq):
     assert rel(got, oracle.schur(U, None, None, kappa, psi)) < 1e-13
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("prec", ["f32", "f16", "f16spinors", "bf16links"])
 def test_multi_rhs_matches_single(lq, prec):
-    """nrhs fields in one launch give bit-identical results to one per call."""
+    """nrhs fields in one launch give bit-identical results to one per call,
+    for the hopping term and for the Schur operator (A^{-1} and x-pay
+    epilogues), plain and dagger."""
     import torch
     dims = (8, 4, 4, 8)
-    R = 3
+    R = 5
+    kappa, csw = 0.13, 1.0
     U = gauge(dims, "smooth", seed=13)
     psis = synth.gaussian_spinor(dims, 14, nfields=R)
     lat = lq.Lattice(dims, max_nrhs=R)
     lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
     fb = lat.field_bytes(prec)
     fin = lat.new_field(prec, nrhs=R)
     fout = lat.new_field(prec, nrhs=R)
-    lat.pack(fin, psis, 1, prec, nrhs=R)
-    lat.dslash(fout, fin, 0, prec=prec, nrhs=R)
     single = torch.empty(fb, dtype=torch.uint8, device="cuda")
-    for r in range(R):
-        lat.dslash(single, fin[r * fb:(r + 1) * fb], 0, prec=prec)
-        torch.cuda.synchronize()
-        assert torch.equal(single, fout[r * fb:(r + 1) * fb])
+    for par in (0, 1):
+        lat.pack(fin, psis, 1 - par, prec, nrhs=R)
+        for dag in (False, True):
+            lat.dslash(fout, fin, par, prec=prec, nrhs=R, dag=dag)
+            for r in range(R):
+                lat.dslash(single, fin[r * fb:(r + 1) * fb], par, prec=prec, dag=dag)
+                torch.cuda.synchronize()
+                assert torch.equal(single, fout[r * fb:(r + 1) * fb]), ("hop", par, dag, r)
+    lat.pack(fin, psis, 1, prec, nrhs=R)
+    for dag in (False, True):
+        lat.dslash(fout, fin, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec, nrhs=R)
+        for r in range(R):
+            lat.dslash(single, fin[r * fb:(r + 1) * fb], 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(single, fout[r * fb:(r + 1) * fb]), ("schur", dag, r)
 
 
 def test_pack_roundtrip(lq):

@@ -115,6 +115,10 @@ def test_eo_cg_16c32_fp32(lq):
 
 
 def test_multi_rhs_and_graph(lq):
+    """Three right-hand sides solved together (fused CG update and norm
+    epilogues on all of them in each launch), with and without graph replay,
+    for 16-bit, FP32 and FP16-spinor inner storage; every solution checked by
+    the oracle."""
     dims = (8, 8, 8, 8)
     kappa, csw = 0.13, 1.0
     R = 3
@@ -127,14 +131,14 @@ def test_multi_rhs_and_graph(lq):
     A = oracle.clover(U, kappa, csw)
     bt = torch.from_numpy(b).cuda()
     torch.cuda.synchronize()
-    for graph in (0, 1):
+    for inner, graph in (("f16", 0), ("f16", 1), ("f32", 1), ("f16spinors", 1)):
         x = lat.canonical_spinor(nrhs=R)
         torch.cuda.synchronize()
-        _, st = lat.solve(x, bt, 1e-10, nrhs=R, inner_prec="f16", use_graph=graph)
+        _, st = lat.solve(x, bt, 1e-10, nrhs=R, inner_prec=inner, use_graph=graph)
         xs = x.cpu().numpy()
         for r in range(R):
             check_solution(U, A, kappa, b[r], xs[r])
-        print("multi-rhs graph=%d: %d iters" % (graph, st["iterations"]))
+        print("multi-rhs %s graph=%d: %d iters" % (inner, graph, st["iterations"]))
 
 
 def test_host_buffers(lq):
