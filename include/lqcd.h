@@ -114,11 +114,23 @@ typedef struct {
     int max_nrhs;         /* largest nrhs used with the solver vectors (>= 1) */
     int gcr_nkrylov;      /* Krylov space of FGCR / FGMRES-DR, 0..256 (0: no vectors
                              reserved; 2 gcr_nkrylov + 3 FP32 full fields otherwise) */
+    int part[4];          /* sub-domains of the global lattice along x, y, z, t (0 or 1:
+                             not cut); dims are then this sub-domain's extents */
+    int coord[4];         /* this sub-domain's position, 0 <= coord < part */
 } lqcd_config;
 
 /* Create a context for one lattice.  `cuda_stream` is a cudaStream_t (may
  * be NULL for the legacy default stream).  No device memory is touched
- * until lqcd_set_workspace. */
+ * until lqcd_set_workspace.
+ *
+ * Sub-domains (the data-parallel split of one lattice over several GPUs, Sec.
+ * 5's multi-node layout): with part[mu] > 1 the context holds the sub-domain
+ * coord of a global lattice of dims[mu] x part[mu] sites along mu (every
+ * local extent even, so that local and global parities agree).  Its links
+ * are the sub-domain's own (canonical layout over the local sites); hops
+ * across a cut boundary go through faces (lqcd_halo_*).  A cut context
+ * supports gauge load, pack / unpack, clover_compute with csw = 0,
+ * lqcd_halo_* and lqcd_norm2; every other call returns LQCD_ERR_STATE. */
 lqcd_status lqcd_create(const lqcd_config* cfg, void* cuda_stream, lqcd_ctx** out);
 lqcd_status lqcd_destroy(lqcd_ctx* ctx);
 lqcd_status lqcd_set_stream(lqcd_ctx* ctx, void* cuda_stream);
@@ -394,6 +406,61 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
  * columns.  1 <= k <= nz <= 256.  LQCD_ERR_BREAKDOWN if Hsq is singular or
  * the eigenvalue iteration does not converge.  Needs no GPU. */
 lqcd_status lqcd_harmonic_ritz(int nz, const double* hbar, int ldh, int k, double* theta, double* g);
+
+/* ---------------------------------------------------------------------
+ * Halo exchange of a sub-domain context (part[mu] > 1 in some direction).
+ * The hopping term of a cut lattice needs, for every output site next to a
+ * cut boundary, the spin-projected neighbour across it: 12 reals (two colour
+ * vectors) per face site and direction, half of a spinor.
+ *
+ * Face buffers: for each cut mu in increasing order, two segments, side 0
+ * then side 1, each at a 256-byte aligned offset (lqcd_halo_layout), of
+ * F/2 face sites x 12 reals (FP64 for LQCD_F64, FP32 for LQCD_F32), F =
+ * local volume / dims[mu]; structure of arrays over the face sites (F64: 6
+ * chunks of double2, F32: 3 chunks of float4).  A face site is indexed by
+ * its three coordinates other than mu, lexicographic with the lowest
+ * direction fastest, halved (the sites of one parity).  nrhs buffer sets
+ * are stored back to back, lqcd_halo_layout's total apart.
+ *
+ * Exchange: the send segment (mu, 0) goes to the backward neighbour along
+ * mu (coord - 1, periodic) and lands in its receive segment (mu, 0); the
+ * send segment (mu, 1) goes to the forward neighbour (coord + 1) and lands
+ * in its receive segment (mu, 1).  Receive side 0 thus holds the forward
+ * hops of the local last slice, side 1 the backward hops of the first.
+ * The fermion sign of hops across the global t boundary is applied by the
+ * receiver.  Only LQCD_F64 and LQCD_F32 storage. */
+
+/* Byte offsets and lengths of the segments [2 mu + side] of one buffer set
+ * (0 for uncut directions) and the set's total size per right-hand side. */
+lqcd_status lqcd_halo_layout(const lqcd_ctx* ctx, lqcd_prec prec, size_t off[8], size_t len[8], size_t* total);
+
+/* Send faces of nrhs internal fields `in` of parity `parity` (the parity
+ * the hopping term reads) for lqcd_halo_dslash with the same dag: segment
+ * (mu, 0) = P psi on the local first slice along mu (the projector of the
+ * forward hop), segment (mu, 1) = U_mu^dag P psi on the last slice (the
+ * backward hop's projector and this sub-domain's own link).  send: device,
+ * nrhs x total bytes.  Asynchronous on the stream. */
+lqcd_status lqcd_halo_pack(lqcd_ctx* ctx, void* send, const void* in, int parity, int dag, lqcd_prec prec,
+                           int nrhs);
+
+/* The hopping term of a sub-domain with an epilogue, out_p = epi(H_{p,1-p} in):
+ *   epi 0: out = a H in;  epi 1: out = a A_pp^{-1} H in;  epi 2: out = A_pp y + a H in
+ * (A = 1: a cut context has no clover term), dag: H^dag.  stage 1 runs the
+ * interior pass (every hop inside the sub-domain; output sites next to a cut
+ * boundary keep a partial sum in out), stage 2 the face pass (adds the faces
+ * of recv to those sites and applies the epilogue), stage 0 both.  Between
+ * the passes the exchange of the faces can run (recv is read only by the
+ * face pass and must hold the neighbours' faces by then).  out, in, y: nrhs
+ * internal fields; recv: nrhs face buffer sets.  out must not alias in or y. */
+lqcd_status lqcd_halo_dslash(lqcd_ctx* ctx, void* out, const void* in, const void* recv, int parity, int dag,
+                             int epi, const void* y, double a, int stage, lqcd_prec prec, int nrhs);
+
+/* FP64 |field|^2 of nrhs internal fields of one parity (parity 0, 1) or
+ * full fields (parity -1) of precision prec, per right-hand side, into
+ * out[nrhs] (host).  On a sub-domain it is the local part of the global sum
+ * (the caller adds the parts, e.g. with an allreduce).  nrhs <= max_nrhs.
+ * Synchronises the stream. */
+lqcd_status lqcd_norm2(lqcd_ctx* ctx, const void* field, int parity, lqcd_prec prec, int nrhs, double* out);
 
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);

@@ -253,6 +253,13 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     if (cfg->max_nrhs < 1 || cfg->max_nrhs > 64) return fail(LQCD_ERR_INVALID, "lqcd_create: max_nrhs must be in [1, 64]");
     if (cfg->gcr_nkrylov < 0 || cfg->gcr_nkrylov > 256)
         return fail(LQCD_ERR_INVALID, "lqcd_create: gcr_nkrylov must be in [0, 256]");
+    int part = 0;
+    for (int m = 0; m < 4; ++m) {
+        const int pm = cfg->part[m] < 1 ? 1 : cfg->part[m];
+        if (cfg->coord[m] < 0 || cfg->coord[m] >= pm)
+            return fail(LQCD_ERR_INVALID, "lqcd_create: need 0 <= coord < part in every direction");
+        if (pm > 1) part |= 1 << m;
+    }
     lqcd_ctx* c = new lqcd_ctx();
     memset(c, 0, sizeof(*c));
     c->cfg = *cfg;
@@ -264,6 +271,9 @@ lqcd_status lqcd_create(const lqcd_config* cfg, void* stream, lqcd_ctx** out)
     c->g.Vh = (int)(V / 2);
     c->g.stride = (c->g.Vh + 127) / 128 * 128;
     c->g.tanti = cfg->t_antiperiodic ? 1 : 0;
+    c->g.part = part;
+    c->g.tfirst = (part >> 3) & 1 ? (cfg->coord[3] == 0) : 1;
+    c->g.tlast = (part >> 3) & 1 ? (cfg->coord[3] == cfg->part[3] - 1) : 1;
     c->block = DSLASH_MAX_BLOCK;
     if (const char* eb = getenv("LQCD_DSLASH_BLOCK")) {  // experiments: threads per dslash block
         const int b = atoi(eb);
@@ -453,6 +463,9 @@ lqcd_status lqcd_clover_compute(lqcd_ctx* c, double kappa, double csw)
     LQ_TRY(check_ready(c));
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_clover_compute: no gauge field loaded");
     if (!(kappa > 0.0) || !(csw >= 0.0)) return fail(LQCD_ERR_INVALID, "lqcd_clover_compute: need kappa > 0, csw >= 0");
+    if (c->cut() && csw != 0.0)
+        return fail(LQCD_ERR_STATE, "lqcd_clover_compute: the clover leaves of a sub-domain need its neighbours' links "
+                                    "(csw = 0 only)");
     DeviceScope dev_scope;
     LQ_TRY(dev_scope.enter(c->device));
     c->kappa = kappa;
@@ -537,6 +550,7 @@ lqcd_status lqcd_dslash(lqcd_ctx* c, void* out, const void* in, int parity, doub
     LQ_TRY(check_ready(c));
     LQ_TRY(check_prec(c, prec));
     if (!out || !in) return fail(LQCD_ERR_INVALID, "lqcd_dslash: null field");
+    if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_dslash: not on a sub-domain of a cut lattice (use lqcd_halo_*)");
     if (out == in) return fail(LQCD_ERR_INVALID, "lqcd_dslash: out must not alias in");
     if (nrhs < 1) return fail(LQCD_ERR_INVALID, "lqcd_dslash: nrhs must be >= 1");
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_dslash: no gauge field loaded");
@@ -579,6 +593,7 @@ lqcd_status lqcd_training_pair(lqcd_ctx* c, float* r, float* e, const double* xs
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     if (!r || !e || !xstar) return fail(LQCD_ERR_INVALID, "lqcd_training_pair: null field");
+    if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_training_pair: not on a sub-domain of a cut lattice (use lqcd_halo_*)");
     if (nrhs < 1) return fail(LQCD_ERR_INVALID, "lqcd_training_pair: nrhs must be >= 1");
     if (!c->gauge_loaded || !c->clover_state)
         return fail(LQCD_ERR_STATE, "lqcd_training_pair: load the gauge field and call lqcd_clover_compute first");
@@ -648,6 +663,7 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
         if (!x[i] || !b[i] || !(tol[i] > 0.0)) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: bad vector or tol");
         if (!c->gauge_loaded || !c->clover_state) return fail(LQCD_ERR_STATE, "lqcd_solve_batch: gauge and clover first");
         if (c->device != ctxs[0]->device) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: contexts on different GPUs");
+        if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_solve_batch: not on a sub-domain of a cut lattice");
         LQ_TRY(check_prec(c, p.inner_prec));
         memset(&stats[i], 0, sizeof(stats[i]));
     }
@@ -663,6 +679,7 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_s
     LQ_TRY(check_ready(c));
     LQ_TRY(check_prec(c, prec));
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_tune: no gauge field loaded");
+    if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_tune: not on a sub-domain of a cut lattice (use lqcd_halo_*)");
     DeviceScope dev_scope;
     LQ_TRY(dev_scope.enter(c->device));
     // scratch: two full fields of the FP64-sized solver vectors, filled with
@@ -766,6 +783,7 @@ lqcd_status lqcd_solve(lqcd_ctx* c, double* x, const double* b, double tol, int 
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     if (!x || !b) return fail(LQCD_ERR_INVALID, "lqcd_solve: null vector");
+    if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_solve: not on a sub-domain of a cut lattice (use lqcd_halo_*)");
     if (nrhs < 1 || nrhs > c->cfg.max_nrhs) return fail(LQCD_ERR_INVALID, "lqcd_solve: nrhs out of range");
     if (!(tol > 0.0)) return fail(LQCD_ERR_INVALID, "lqcd_solve: tol must be > 0");
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_solve: no gauge field loaded");

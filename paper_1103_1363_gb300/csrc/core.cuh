@@ -122,6 +122,9 @@ struct Geom {
     int Vh;      // sites per parity
     int stride;  // Vh rounded up to a multiple of 128
     int tanti;   // antiperiodic fermion boundary in t
+    int part;    // bit mu: the global lattice is cut along mu; hops across the local boundary use faces
+    int tfirst;  // this sub-domain holds the global t = 0 slice (fermion sign on its backward t faces)
+    int tlast;   // ... the global t = Lt - 1 slice (sign on its forward t faces)
 };
 
 // ----------------------------------------------------------------- helpers

@@ -156,7 +156,9 @@ __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[1
 
 // PG: storage of links and clover; PS: storage of spinor fields; the
 // arithmetic is in RealT<PS> (FP64 only when everything is FP64).
-template <int PG, int PS, int RECON, int MU, bool DAG>
+// HALO (sub-domain interior pass): a hop across the local boundary of a
+// cut direction is left out; it arrives later as a face.
+template <int PG, int PS, int RECON, int MU, bool DAG, bool HALO = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int i, int full, const int c[4],
                                         int stepmu, typename RealT<PS>::type acc[24])
 {
@@ -165,27 +167,32 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
     const int fwd = (c[MU] == L - 1) ? full - (L - 1) * stepmu : full + stepmu;
     const int bwd = (c[MU] == 0) ? full + (L - 1) * stepmu : full - stepmu;
     const bool tb = (MU == 3) && A.g.tanti;
+    const bool cut = HALO && ((A.g.part >> MU) & 1);
     R v[24], h[12], u[18], w[12];
     // forward: (1 - g) U_mu(x) in(x + mu)   [dagger: (1 + g)]
-    SpinorIO<PS>::load(in, A.g.stride, fwd >> 1, v);
-    project<MU, DAG ? +1 : -1>(v, h);
-    if (tb && c[3] == L - 1) {
+    if (!(cut && c[MU] == L - 1)) {
+        SpinorIO<PS>::load(in, A.g.stride, fwd >> 1, v);
+        project<MU, DAG ? +1 : -1>(v, h);
+        if (tb && c[3] == L - 1) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) h[k] = -h[k];
+            for (int k = 0; k < 12; ++k) h[k] = -h[k];
+        }
+        GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
+        su3_mul_half<false>(u, h, w);
+        accumulate<MU, DAG ? +1 : -1>(acc, w);
     }
-    GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
-    su3_mul_half<false>(u, h, w);
-    accumulate<MU, DAG ? +1 : -1>(acc, w);
     // backward: (1 + g) U_mu(x - mu)^dag in(x - mu)   [dagger: (1 - g)]
-    SpinorIO<PS>::load(in, A.g.stride, bwd >> 1, v);
-    project<MU, DAG ? -1 : +1>(v, h);
-    if (tb && c[3] == 0) {
+    if (!(cut && c[MU] == 0)) {
+        SpinorIO<PS>::load(in, A.g.stride, bwd >> 1, v);
+        project<MU, DAG ? -1 : +1>(v, h);
+        if (tb && c[3] == 0) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) h[k] = -h[k];
+            for (int k = 0; k < 12; ++k) h[k] = -h[k];
+        }
+        GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
+        su3_mul_half<true>(u, h, w);
+        accumulate<MU, DAG ? -1 : +1>(acc, w);
     }
-    GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
-    su3_mul_half<true>(u, h, w);
-    accumulate<MU, DAG ? -1 : +1>(acc, w);
 }
 
 // ---- software-pipelined gather for half-precision spinors + recon-12 links
@@ -371,9 +378,21 @@ __device__ __forceinline__ void dslash_epilogue(const DslashArgs& A, int rhs, in
     }
 }
 
+// True if site c of a sub-domain has a neighbour across a cut boundary.
+__device__ __forceinline__ bool on_cut_face(const Geom& g, const int c[4])
+{
+    bool f = false;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+        if (((g.part >> mu) & 1) && (c[mu] == 0 || c[mu] == g.L[mu] - 1)) f = true;
+    return f;
+}
+
 // The hopping term and epilogue at output site i of right-hand side rhs;
-// nrm accumulates |out|^2 (|r|^2 for EPI_CG).
-template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
+// nrm accumulates |out|^2 (|r|^2 for EPI_CG).  HALO: the interior pass of a
+// sub-domain; a site with a neighbour across a cut boundary stores its
+// partial sum unfinished (no epilogue) for the face pass to complete.
+template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED, bool HALO = false>
 __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i, double& nrm)
 {
     typedef typename RealT<PS>::type R;
@@ -385,12 +404,17 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i,
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
     if constexpr ((PS == P16 || PS == PB16) && PG == PS) {
+        static_assert(!HALO, "sub-domain hops use the generic gather");
         hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG>(A, in, i, full, c, acc);
     } else {
-        hop_dir<PG, PS, RECON, 0, DAG>(A, in, i, full, c, 1, acc);
-        hop_dir<PG, PS, RECON, 1, DAG>(A, in, i, full, c, A.g.L[0], acc);
-        hop_dir<PG, PS, RECON, 2, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
-        hop_dir<PG, PS, RECON, 3, DAG>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+        hop_dir<PG, PS, RECON, 0, DAG, HALO>(A, in, i, full, c, 1, acc);
+        hop_dir<PG, PS, RECON, 1, DAG, HALO>(A, in, i, full, c, A.g.L[0], acc);
+        hop_dir<PG, PS, RECON, 2, DAG, HALO>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
+        hop_dir<PG, PS, RECON, 3, DAG, HALO>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+    }
+    if (HALO && on_cut_face(A.g, c)) {
+        SpinorIO<PS>::store(static_cast<char*>(A.out) + rhs * A.out_rb, A.g.stride, i, acc);
+        return;
     }
     dslash_epilogue<PG, PS, DAG, EPI, RED>(A, rhs, i, acc, nrm);
 }

@@ -195,6 +195,8 @@ struct lqcd_ctx {
         return (size_t)g.stride * lqcd::gauge_link_bytes(P, P == lqcd::P64 ? 18 : cfg.recon);
     }
     int recon_of(int P) const { return P == lqcd::P64 ? 18 : cfg.recon; }
+    // is this context a sub-domain of a cut lattice?
+    bool cut() const { return g.part != 0; }
     // does the context hold links and clover for storage precision P (0..3)?
     bool holds(int P) const { return P == lqcd::P64 || (cfg.prec_mask >> P) & 1; }
 };

@@ -1323,6 +1323,7 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
             if (channels[l] < 1 || channels[l] > NET_MAXC) return fail(LQCD_ERR_INVALID, "lqcd_net_create: widths in [1, 12]");
         if (max_batch < 1) return fail(LQCD_ERR_INVALID, "lqcd_net_create: max_batch >= 1");
         if (!c->holds(P32)) return fail(LQCD_ERR_STATE, "lqcd_net_create: the context must hold F32 links");
+        if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_net_create: not on a sub-domain of a cut lattice");
         lqcd_net* n = new lqcd_net();
         memset(n, 0, sizeof(*n));
         n->ctx = c;

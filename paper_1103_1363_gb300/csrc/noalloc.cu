@@ -49,6 +49,7 @@ extern "C" lqcd_status lqcd_dslash_schur_static(lqcd_ctx* c, void* out, const vo
         if (out == in) return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: out must not alias in");
         if (nrhs < 1) return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: nrhs must be >= 1");
         if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_dslash_schur_static: no gauge field loaded");
+        if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_dslash_schur_static: not on a sub-domain of a cut lattice");
         const double have_csw = c->clover_state ? c->csw : 0.0;
         if (csw != have_csw) return fail(LQCD_ERR_STATE, "lqcd_dslash_schur_static: csw differs from lqcd_clover_compute");
         if (csw != 0.0 && kappa != c->kappa) return fail(LQCD_ERR_STATE, "lqcd_dslash_schur_static: kappa differs from lqcd_clover_compute");

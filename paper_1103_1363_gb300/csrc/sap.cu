@@ -554,6 +554,7 @@ lqcd_status lqcd_sap_apply(lqcd_ctx* c, void* z, const void* r, const int block[
     if (!c || !z || !r || !block) return fail(LQCD_ERR_INVALID, "lqcd_sap_apply: null argument");
     if (!c->ws) return fail(LQCD_ERR_NOMEM, "no workspace: call lqcd_set_workspace");
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_sap_apply: no gauge field loaded");
+    if (c->cut()) return fail(LQCD_ERR_STATE, "lqcd_sap_apply: not on a sub-domain of a cut lattice");
     if (ncycle < 1 || nmr < 1) return fail(LQCD_ERR_INVALID, "lqcd_sap_apply: ncycle and nmr must be >= 1");
     DeviceScope dev_scope;
     LQ_TRY(dev_scope.enter(c->device));

@@ -41,7 +41,8 @@ SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR, SOLVER_FGMRES_DR = 0, 1, 2, 3
 
 class lqcd_config(C.Structure):
     _fields_ = [("dims", C.c_int * 4), ("t_antiperiodic", C.c_int), ("recon", C.c_int),
-                ("prec_mask", C.c_int), ("max_nrhs", C.c_int), ("gcr_nkrylov", C.c_int)]
+                ("prec_mask", C.c_int), ("max_nrhs", C.c_int), ("gcr_nkrylov", C.c_int),
+                ("part", C.c_int * 4), ("coord", C.c_int * 4)]
 
 
 class lqcd_solver_params(C.Structure):
@@ -89,6 +90,10 @@ _SIGS = {
     "lqcd_dslash_schur_static": [_P, _P, _P, _D, _D, _I, _I, _I],
     "lqcd_set_preconditioner": [_P, _P],
     "lqcd_training_pair": [_P, _P, _P, _P, _P, _I],
+    "lqcd_halo_layout": [_P, _I, C.POINTER(_S), C.POINTER(_S), C.POINTER(_S)],
+    "lqcd_halo_pack": [_P, _P, _P, _I, _I, _I, _I],
+    "lqcd_halo_dslash": [_P, _P, _P, _P, _I, _I, _I, _P, _D, _I, _I, _I],
+    "lqcd_norm2": [_P, _P, _I, _I, _I, C.POINTER(_D)],
     "lqcd_set_preconditioner_sap": [_P, _P, _I, _I],
     "lqcd_harmonic_ritz": [_I, _P, _I, _I, _P, _P],
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
@@ -166,8 +171,11 @@ def lqcd_last_error():
 
 
 def lqcd_create(dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16"),
-                max_nrhs=1, gcr_nkrylov=0, stream=None):
+                max_nrhs=1, gcr_nkrylov=0, stream=None, part=(1, 1, 1, 1), coord=(0, 0, 0, 0)):
     cfg = lqcd_config()
+    for i in range(4):
+        cfg.part[i] = int(part[i])
+        cfg.coord[i] = int(coord[i])
     for i, d in enumerate(dims):
         cfg.dims[i] = int(d)
     cfg.t_antiperiodic = int(t_antiperiodic)
@@ -242,6 +250,30 @@ def lqcd_training_pair(ctx, r, e, xstar, x=None, nrhs=1):
     """e = x* - x, r = M e as canonical FP32 complex spinors (device)."""
     _check(_lib.lqcd_training_pair(ctx, _ptr(r), _ptr(e), _ptr(xstar), _ptr(x) if x is not None else None,
                                    int(nrhs)), "lqcd_training_pair")
+
+
+def lqcd_halo_layout(ctx, prec):
+    """(offsets[8], lengths[8], total) of a face buffer set, segment 2 mu + side."""
+    off, ln, tot = (C.c_size_t * 8)(), (C.c_size_t * 8)(), C.c_size_t()
+    _check(_lib.lqcd_halo_layout(ctx, PREC.get(prec, prec), off, ln, C.byref(tot)), "lqcd_halo_layout")
+    return list(off), list(ln), tot.value
+
+
+def lqcd_halo_pack(ctx, send, inp, parity, dag, prec, nrhs=1):
+    _check(_lib.lqcd_halo_pack(ctx, _ptr(send), _ptr(inp), int(parity), int(bool(dag)), PREC.get(prec, prec),
+                               int(nrhs)), "lqcd_halo_pack")
+
+
+def lqcd_halo_dslash(ctx, out, inp, recv, parity, dag=False, epi=0, y=None, a=1.0, stage=0, prec="f32", nrhs=1):
+    _check(_lib.lqcd_halo_dslash(ctx, _ptr(out), _ptr(inp), _ptr(recv) if recv is not None else None, int(parity),
+                                 int(bool(dag)), int(epi), _ptr(y) if y is not None else None, float(a), int(stage),
+                                 PREC.get(prec, prec), int(nrhs)), "lqcd_halo_dslash")
+
+
+def lqcd_norm2(ctx, field, parity, prec, nrhs=1):
+    out = (C.c_double * nrhs)()
+    _check(_lib.lqcd_norm2(ctx, _ptr(field), int(parity), PREC.get(prec, prec), int(nrhs), out), "lqcd_norm2")
+    return list(out)
 
 
 def lqcd_clover_apply(ctx, out, inp, parity, inverse, prec, nrhs=1):
@@ -447,13 +479,14 @@ class Lattice:
 
     def __init__(self, dims, t_antiperiodic=1, recon=12, precisions=("f64", "f32", "f16", "bf16",
                                                                      "f16links", "bf16links"),
-                 max_nrhs=1, gcr_nkrylov=0, device="cuda", stream=None):
+                 max_nrhs=1, gcr_nkrylov=0, device="cuda", stream=None, part=(1, 1, 1, 1),
+                 coord=(0, 0, 0, 0)):
         self.dims = tuple(int(d) for d in dims)
         self.device = torch.device(device)
         self.stream = stream
         with torch.cuda.device(self.device):
             self.ctx = lqcd_create(self.dims, t_antiperiodic, recon, precisions, max_nrhs,
-                                   gcr_nkrylov, stream)
+                                   gcr_nkrylov, stream, part, coord)
             n = lqcd_workspace_size(self.ctx)
             self.workspace = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
             off = (-self.workspace.data_ptr()) % 256
