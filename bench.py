@@ -52,7 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 # from one ncu capture of a CG iteration on 24^3x48 (the four launches of an
 # iteration: Mhat sweeps with A^-1 and x-pay + norm epilogues, Mhat^dag sweeps
 # with A^-1 and the fused CG update); traffic grows with the sites processed.
-DRAM_BYTES_PER_SITE = {"f16spinors": (766.2 + 827.6 + 766.2 + 1165.1) / 4}
+DRAM_BYTES_PER_SITE = {"f16spinors": (766.4 + 820.0 + 766.4 + 1150.9) / 4}
 STORAGE = {
     "f32": "f32 spinors, links (recon-12) and clover",
     "f16": "f16 spinors (per-site norm), links (recon-12) and clover",
