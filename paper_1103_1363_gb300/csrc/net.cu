@@ -57,6 +57,10 @@ struct NetLayerArgs {
     int batch;         // tensor-core path: batch items (tiles are strided over batch x sites)
     int tmem_cols;     // tensor-core path: allocated tensor-memory columns (power of 2 >= 3 N2p)
     int* errw;         // device error word (bounded waits that expire set ERRW_TIMEOUT)
+    int in_bf16;       // activations in BF16 planes (else FP32): the BF16 network's multi-channel ones
+    int out_bf16;
+    int gout_bf16;     // weight gradient: the output gradient in BF16 planes
+    int nhops;         // tensor-core layer: hops 0 .. nhops - 1 (9; 1 for the stacked contraction)
 };
 
 __host__ __device__ inline int adj_hop(int h) { return h == 0 ? 0 : (h % 2 == 1 ? h + 1 : h - 1); }
@@ -322,6 +326,33 @@ __device__ __forceinline__ int hop_neighbour(const NetLayerArgs& a, int x, int c
     return fwd ? (cm == Lm - 1 ? x - (Lm - 1) * st : x + st) : (cm == 0 ? x + (Lm - 1) * st : x - st);
 }
 
+// Batch item b of planar activations with ch channels: FP32 (six float4
+// planes per channel, 96 bytes per channel and site) or BF16 (three planes of
+// eight BF16 values, i.e. four complex, per channel: 48 bytes).
+__host__ __device__ inline size_t act_item_bytes(int V, int ch, int bf) { return (size_t)V * ch * (bf ? 48 : 96); }
+
+// The 24 floats of channel ci at site y of BF16 planar activations of one
+// item (zeros for y < 0).  BF16 is the upper half of FP32: a shift converts.
+__device__ __forceinline__ void load_channel_bf16(const uint4* in_b, int V, int ci, int y, float p[24])
+{
+    if (y >= 0) {
+        const uint4* src = in_b + (size_t)ci * 3 * V + y;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const uint4 v = __ldg(src + (size_t)q * V);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                p[8 * q + 2 * m] = __uint_as_float(w[m] << 16);
+                p[8 * q + 2 * m + 1] = __uint_as_float(w[m] & 0xffff0000u);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 24; ++q) p[q] = 0.f;
+    }
+}
+
 // The 24 floats of channel ci at site y of planar activations (zeros for y < 0).
 __device__ __forceinline__ void load_channel(const float* in_b, int V, int ci, int y, float p[24])
 {
@@ -338,6 +369,14 @@ __device__ __forceinline__ void load_channel(const float* in_b, int V, int ci, i
     }
 }
 
+// Channel ci at site y of batch item b of activations `act` (FP32 or BF16 planes).
+__device__ __forceinline__ void load_act(const void* act, int bf, int V, int ch, int b, int ci, int y, float p[24])
+{
+    const char* item = static_cast<const char*>(act) + (size_t)b * act_item_bytes(V, ch, bf);
+    if (bf) load_channel_bf16(reinterpret_cast<const uint4*>(item), V, ci, y, p);
+    else load_channel(reinterpret_cast<const float*>(item), V, ci, y, p);
+}
+
 // Upper bound of any wait on this kernel's own MMAs (a hop's MMAs take
 // microseconds); an expired wait sets ERRW_TIMEOUT and the CTA stops.
 #define NTC_WAIT_NS 2000000000ull
@@ -350,7 +389,9 @@ __device__ __forceinline__ void load_channel(const float* in_b, int V, int ci, i
 // mbarriers (MMAs of stage s done, B_h of stage s landed) and the
 // tensor-memory address.  Thread (site sl = tid % 128, group grp = tid /
 // 128): group 0 stages hop h+1's links while groups 1-3 gather hop h
-// (channels grp - 1 + 3 j; hop 0, the identity, needs no link).  B_h
+// (channels grp - 1 + 3 j; hop 0, the identity, needs no link; giving group
+// 0 channels too was measured slower: 180 against 164 us for the 12 -> 12
+// layer at 16^4).  B_h
 // arrives by one bulk copy per hop.  Tensor memory: the accumulator of
 // colour a in columns [a N2p, (a+1) N2p), lane = site of the tile.
 template <int RECON>
@@ -397,24 +438,23 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
     float nxt[24];
     if ((int)blockIdx.x < total && nj > 0) {
         const int t = blockIdx.x, b = t / ntiles, x0 = (t - b * ntiles) * NTC_TS + sl;
-        load_channel(a.in + (size_t)b * a.V * a.cin * 24, a.V, cfirst, x0 < a.V ? x0 : -1, nxt);
+        load_act(a.in, a.in_bf16, a.V, a.cin, b, cfirst, x0 < a.V ? x0 : -1, nxt);
     }
     bool wait_failed = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int b = t / ntiles, tile0 = (t - b * ntiles) * NTC_TS;
-        const float* in_b = a.in + (size_t)b * a.V * a.cin * 24;
         const int x = tile0 + sl;
         const int c0 = x % a.L[0], c1 = (x / a.L[0]) % a.L[1], c2 = (x / (a.L[0] * a.L[1])) % a.L[2],
                   c3 = x / (a.L[0] * a.L[1] * a.L[2]);
         const int tn = t + gridDim.x;  // this CTA's next tile
-        for (int h = 0; h < 9; ++h) {
+        for (int h = 0; h < a.nhops; ++h) {
             const int s = g & 1;
             unsigned char* const Xst = smem + s * xbytes;               // stage s: X
             unsigned char* const Bst = smem + 2 * xbytes + s * bbytes;  // stage s: B_h
             // stage s is free once the MMAs of hop g - 2 have completed (each
             // thread waits for itself; a failure is shared at the barrier below)
             if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, NTC_WAIT_NS);
-            if (grp == 0 && h < 8) {  // links of hop h + 1 (read after this hop's barrier)
+            if (grp == 0 && h + 1 < a.nhops) {  // links of hop h + 1 (read after this hop's barrier)
                 float un[18];
                 float sign = 1.f;
                 if (x < a.V) {
@@ -448,12 +488,13 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
 #pragma unroll
                 for (int q = 0; q < 24; ++q) cur[q] = nxt[q];
                 if (j + 1 < nj) {
-                    load_channel(in_b, a.V, ci + TG, yh, nxt);
-                } else if (h < 8) {
-                    load_channel(in_b, a.V, cfirst, x < a.V ? hop_neighbour(a, x, c0, c1, c2, c3, h + 1) : -1, nxt);
+                    load_act(a.in, a.in_bf16, a.V, a.cin, b, ci + TG, yh, nxt);
+                } else if (h + 1 < a.nhops) {
+                    load_act(a.in, a.in_bf16, a.V, a.cin, b, cfirst,
+                             x < a.V ? hop_neighbour(a, x, c0, c1, c2, c3, h + 1) : -1, nxt);
                 } else if (tn < total) {
                     const int bn = tn / ntiles, xn = (tn - bn * ntiles) * NTC_TS + sl;
-                    load_channel(a.in + (size_t)bn * a.V * a.cin * 24, a.V, cfirst, xn < a.V ? xn : -1, nxt);
+                    load_act(a.in, a.in_bf16, a.V, a.cin, bn, cfirst, xn < a.V ? xn : -1, nxt);
                 }
 #pragma unroll
                 for (int ca = 0; ca < 3; ++ca) {
@@ -468,11 +509,13 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
                             re = 0.f;
                             im = 0.f;
 #pragma unroll
-                            for (int cb = 0; cb < 3; ++cb) {
+                            for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
                                 const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
                                 const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
-                                re += ur * pr - ui * pi;
-                                im += ur * pi + ui * pr;
+                                re += ur * pr;
+                                re -= ui * pi;
+                                im += ur * pi;
+                                im += ui * pr;
                             }
                         }
                         w[r] = pack_bf16x2(re, im);
@@ -515,7 +558,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
         const int q4 = warp & 3, wg = warp >> 2;
         const int site = tile0 + 32 * q4 + lane;
         const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
-        float4* out_b = reinterpret_cast<float4*>(a.out) + (size_t)b * a.V * a.cout * 6;
+        char* out_item = static_cast<char*>(static_cast<void*>(a.out)) + (size_t)b * act_item_bytes(a.V, a.cout, a.out_bf16);
         for (int c0 = 16 * wg; c0 < N2p; c0 += 16 * (NTC_THREADS / 128)) {
             uint32_t v[3][16];
 #pragma unroll
@@ -526,14 +569,30 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
                 for (int hc = 0; hc < 2; ++hc) {
                     const int co = c0 / 8 + hc;
                     if (co >= a.cout) break;
+                    if (a.out_bf16) {
+                        uint4* ob = reinterpret_cast<uint4*>(out_item) + (size_t)co * 3 * a.V + site;
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        // complex k = 2q, 2q+1 of channel co: spin k / 3, colour k % 3
-                        const int k0 = 2 * q, k1 = 2 * q + 1;
-                        const int j0 = 4 * hc + k0 / 3, j1 = 4 * hc + k1 / 3;
-                        out_b[plane4(a.V, co, q) + site] =
-                            make_float4(__uint_as_float(v[k0 % 3][2 * j0]), __uint_as_float(v[k0 % 3][2 * j0 + 1]),
-                                        __uint_as_float(v[k1 % 3][2 * j1]), __uint_as_float(v[k1 % 3][2 * j1 + 1]));
+                        for (int q = 0; q < 3; ++q) {
+                            // complex k = 4q .. 4q+3 of channel co: spin k / 3, colour k % 3
+                            uint32_t w[4];
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) {
+                                const int kk = 4 * q + m, j = 4 * hc + kk / 3;
+                                w[m] = pack_bf16x2(__uint_as_float(v[kk % 3][2 * j]), __uint_as_float(v[kk % 3][2 * j + 1]));
+                            }
+                            ob[(size_t)q * a.V] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    } else {
+                        float4* out_b = reinterpret_cast<float4*>(out_item);
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            // complex k = 2q, 2q+1 of channel co: spin k / 3, colour k % 3
+                            const int k0 = 2 * q, k1 = 2 * q + 1;
+                            const int j0 = 4 * hc + k0 / 3, j1 = 4 * hc + k1 / 3;
+                            out_b[plane4(a.V, co, q) + site] = make_float4(
+                                __uint_as_float(v[k0 % 3][2 * j0]), __uint_as_float(v[k0 % 3][2 * j0 + 1]),
+                                __uint_as_float(v[k1 % 3][2 * j1]), __uint_as_float(v[k1 % 3][2 * j1 + 1]));
+                        }
                     }
                 }
             }
@@ -627,9 +686,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_tc_kernel(const NetL
                           c3 = x / (a.L[0] * a.L[1] * a.L[2]);
                 y = hop_neighbour(a, x, c0, c1, c2, c3, h);
             }
-            load_channel(a.in + (size_t)b * a.V * a.cin * 24, a.V, grp + G4 * i, y, p);
+            load_act(a.in, a.in_bf16, a.V, a.cin, b, grp + G4 * i, y, p);
         } else {
-            load_channel(gout + (size_t)b * a.V * a.cout * 24, a.V, grp + G4 * (i - nX), x < a.V ? x : -1, p);
+            load_act(gout, a.gout_bf16, a.V, a.cout, b, grp + G4 * (i - nX), x < a.V ? x : -1, p);
         }
     };
     float nxt[24];
@@ -682,11 +741,13 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_tc_kernel(const NetL
                         re = 0.f;
                         im = 0.f;
 #pragma unroll
-                        for (int cb = 0; cb < 3; ++cb) {
+                        for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
                             const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
                             const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
-                            re += ur * pr - ui * pi;
-                            im += ur * pi + ui * pr;
+                            re += ur * pr;
+                            re -= ui * pi;
+                            im += ur * pi;
+                            im += ui * pr;
                         }
                     }
                     w[r] = pack_bf16x2(re, im);
@@ -901,6 +962,68 @@ __global__ void net_prep_weights_kernel(const float* W, int cin, int cout, int a
     }
 }
 
+// Stacked weights of a layer with one output channel, for the contraction
+// before the transport: one "hop" whose outputs n2' = 8 h + n2 are the nine
+// hops' real-ified outputs (Z_h = W_h in, spin and re / im), BF16 in the same
+// core-matrix order as net_prep_weights_kernel.
+__global__ void net_prep_stacked_kernel(const float* W, int cin, uint16_t* Bh, int K2p, int N2p)
+{
+    const int nk = 4 * cin, K2 = 2 * nk;
+    const int total = N2p * K2p;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int n2s = e / K2p, k2 = e % K2p;
+        float v = 0.f;
+        if (n2s < 72 && k2 < K2) {
+            const int h = n2s / 8, n2 = n2s % 8, n = n2 / 2, k = k2 / 2;
+            const float* w = W + (((size_t)h * 4 + n) * nk + k) * 2;
+            const float wr = w[0], wi = w[1];
+            if ((n2 & 1) == 0) v = (k2 & 1) == 0 ? wr : -wi;
+            else v = (k2 & 1) == 0 ? wi : wr;
+        }
+        Bh[(n2s / 8) * (K2p / 8) * 64 + (k2 / 8) * 64 + (n2s % 8) * 8 + k2 % 8] = f2bf(v);
+    }
+}
+
+// Transport after the contraction for a layer with one output channel:
+// out(x) = Z_0(x) + sum_{h >= 1} U_h(x) Z_h(x + h) (fermion sign included),
+// Z_h = W_h in the stacked contraction's nine BF16 channels.  W_h acts on
+// spin and channel, U_h on colour, so the two commute: four colour vectors
+// are transported per hop instead of 4 C_in.  Output: one FP32 channel.
+template <int RECON>
+__global__ void __launch_bounds__(128) net_gather_transport_kernel(const NetLayerArgs a, const void* z, float* out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (x >= a.V) return;
+    float acc[24];
+    load_act(z, 1, a.V, 9, b, 0, x, acc);
+    for (int h = 1; h < 9; ++h) {
+        float u[18], sign;
+        const int y = hop_link<RECON>(a, x, h, u, sign);
+        float p[24];
+        load_act(z, 1, a.V, 9, b, h, y, p);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
+                    const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                    const float pr = p[2 * (3 * sp + cb)], pi = p[2 * (3 * sp + cb) + 1];
+                    re += ur * pr;
+                    re -= ui * pi;
+                    im += ur * pi;
+                    im += ui * pr;
+                }
+                acc[2 * (3 * sp + ca)] += sign * re;
+                acc[2 * (3 * sp + ca) + 1] += sign * im;
+            }
+    }
+    float4* o = reinterpret_cast<float4*>(out) + (size_t)b * a.V * 6;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[plane4(a.V, 0, q) + x] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+}
+
 // Canonical complex spinor (Cin = 1 activation) <-> internal FP32 full field.
 __global__ void net_from_internal_kernel(Geom g, const char* in, size_t in_rb, float* act, int L0, int nb)
 {
@@ -947,6 +1070,31 @@ __global__ void net_layout_kernel(const float4* src, float4* dst, int V, int ch,
         const size_t can = b * per + (site * ch + cq / 6) * 6 + cq % 6;
         if (to_planar) dst[e] = src[can];
         else dst[can] = src[e];
+    }
+}
+
+// Canonical FP32 <-> BF16 planar: plane q of channel c holds complex 4q .. 4q+3
+// (two canonical float4) of every site, as eight BF16 values.
+__global__ void net_layout_bf16_kernel(const void* src, void* dst, int V, int ch, int nb, int to_planar)
+{
+    const size_t per = (size_t)V * ch * 3, total = per * nb;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / per, r = e - b * per;
+        const size_t site = r % V, cq = r / V;
+        const size_t can = (b * (size_t)V * ch + site * ch + cq / 3) * 6 + 2 * (cq % 3);  // float4 index
+        if (to_planar) {
+            const float4* s4 = static_cast<const float4*>(src);
+            const float4 x = s4[can], y = s4[can + 1];
+            static_cast<uint4*>(dst)[e] = make_uint4(pack_bf16x2(x.x, x.y), pack_bf16x2(x.z, x.w), pack_bf16x2(y.x, y.y),
+                                                     pack_bf16x2(y.z, y.w));
+        } else {
+            const uint4 v = static_cast<const uint4*>(src)[e];
+            float4* d4 = static_cast<float4*>(dst);
+            d4[can] = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                                  __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+            d4[can + 1] = make_float4(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u),
+                                      __uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
+        }
     }
 }
 
@@ -1038,6 +1186,9 @@ struct lqcd_net {
     uint16_t* Bh[8];
     float* BfA[8];         // adjoint (input-gradient) weights
     uint16_t* BhA[8];
+    uint16_t* BhS[8];      // stacked BF16 weights of layers with one output channel (stacked[l])
+    int stacked[8];        // layer l contracts before it transports (BF16, C_out = 1 < C_in)
+    float* zbuf;           // the stacked contraction's nine BF16 channels, max_batch items (any stacked)
     float* act[9];         // planar activations per layer boundary, max_batch items
     float* gact[2];        // gradient ping-pong buffers (max channels)
     double* red;           // loss reductions [max_batch][2]
@@ -1080,6 +1231,9 @@ NetLayerArgs layer_args(const lqcd_net* n, int l, bool adjoint, const float* in,
     while (cols < 3 * a.N2p) cols *= 2;
     a.tmem_cols = cols;
     a.errw = c->errw;
+    a.in_bf16 = n->bf16 && a.cin > 1;   // multi-channel activations of the BF16 network: BF16 planes
+    a.out_bf16 = n->bf16 && a.cout > 1;
+    a.nhops = 9;
     return a;
 }
 
@@ -1111,12 +1265,14 @@ int sm_count()
 // Algorithmic work of one layer launch over `batch` items: the channel
 // contraction (8 real flops per complex multiply-add, 4 C_out x 4 C_in x 3
 // colours x 9 hops per site) and the compulsory bytes (input activations,
-// output activations or gradient, each FP32 link once).
+// output activations or gradient, 96 bytes per channel and site in FP32 or
+// 48 in BF16, each FP32 link once).
 void layer_work(const NetLayerArgs& a, int batch, double& bytes, double& flops)
 {
     const double V = (double)a.V * batch;
     flops = 8.0 * (4.0 * a.cout) * (4.0 * a.cin) * 3.0 * 9.0 * V;
-    bytes = 96.0 * (a.cin + a.cout) * V + 4.0 * gauge_link_bytes(P32, 12) * a.V;
+    bytes = ((a.in_bf16 ? 48.0 : 96.0) * a.cin + (a.out_bf16 ? 48.0 : 96.0) * a.cout) * V +
+            4.0 * gauge_link_bytes(P32, 12) * a.V;
 }
 
 // Event pair around one launch when profiling (not while capturing a graph).
@@ -1137,20 +1293,43 @@ lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch, int prof_i
     layer_work(a, batch, wb, wf);
     NetTimed tm;
     LQ_TRY(tm.begin(n, prof_idx, wb, wf));
+    const int layer = prof_idx / 3, kind = prof_idx % 3;
+    const bool stack = n->bf16 && kind == 0 && n->stacked[layer];
+    NetLayerArgs z = a;  // the stacked contraction: one hop, nine "channels" Z_h = W_h in
+    if (stack) {
+        z.nhops = 1;
+        z.cout = 9;
+        z.N2 = 72;
+        z.N2p = 80;
+        z.Bh = n->BhS[layer];
+        z.out = n->zbuf;
+        z.out_bf16 = 1;
+        int cols = 32;
+        while (cols < 3 * z.N2p) cols *= 2;
+        z.tmem_cols = cols;
+    }
     if (n->bf16) {
         // persistent: one CTA per SM strides over the batch x site tiles
+        const NetLayerArgs& t = stack ? z : a;
         const int sms = sm_count();
         if (sms <= 0) return fail(LQCD_ERR_CUDA, "net layer: no SM count");
-        const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
-        const size_t sm = layer_smem_tc(a);
+        const int total = (t.V + NTC_TS - 1) / NTC_TS * batch;
+        const size_t sm = layer_smem_tc(t);
         int grid = total < sms ? total : sms;
         if (n->max_ctas > 0 && grid > n->max_ctas) grid = n->max_ctas;
         if (c->cfg.recon == 12) {
             LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            net_layer_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(a);
+            net_layer_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(t);
         } else {
             LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            net_layer_tc_kernel<18><<<grid, NTC_THREADS, sm, c->stream>>>(a);
+            net_layer_tc_kernel<18><<<grid, NTC_THREADS, sm, c->stream>>>(t);
+        }
+        if (stack) {  // then the transport of the four colour vectors per hop
+            LQ_CUDA(cudaGetLastError());
+            c->launches++;
+            dim3 g2((a.V + 127) / 128, batch);
+            if (c->cfg.recon == 12) net_gather_transport_kernel<12><<<g2, 128, 0, c->stream>>>(a, n->zbuf, a.out);
+            else net_gather_transport_kernel<18><<<g2, 128, 0, c->stream>>>(a, n->zbuf, a.out);
         }
     } else {
         const size_t sm = layer_smem_f32(a);
@@ -1180,6 +1359,12 @@ lqcd_status prep_weights(lqcd_net* n)
             LQ_CUDA(cudaGetLastError());
             c->launches++;
         }
+    for (int l = 0; l < n->nlayers; ++l) {
+        if (!n->stacked[l]) continue;
+        net_prep_stacked_kernel<<<32, 256, 0, c->stream>>>(n->W + n->woff[l], n->ch[l], n->BhS[l], pad16(8 * n->ch[l]), 80);
+        LQ_CUDA(cudaGetLastError());
+        c->launches++;
+    }
     return LQCD_OK;
 }
 
@@ -1192,8 +1377,11 @@ lqcd_status convert_layout(lqcd_net* n, const float* src, float* dst, int ch, in
     const int V = 2 * c->g.Vh;
     const size_t total = (size_t)V * ch * 6 * batch;
     const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-    net_layout_kernel<<<grid, 256, 0, c->stream>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst),
-                                                   V, ch, batch, to_planar ? 1 : 0);
+    if (n->bf16 && ch > 1)
+        net_layout_bf16_kernel<<<grid, 256, 0, c->stream>>>(src, dst, V, ch, batch, to_planar ? 1 : 0);
+    else
+        net_layout_kernel<<<grid, 256, 0, c->stream>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst),
+                                                       V, ch, batch, to_planar ? 1 : 0);
     LQ_CUDA(cudaGetLastError());
     c->launches++;
     return LQCD_OK;
@@ -1207,6 +1395,7 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
     const size_t nw = n->woff[layer + 1] - n->woff[layer];
     if (zero) LQ_CUDA(cudaMemsetAsync(gl, 0, nw * 4, c->stream));
     NetLayerArgs a = layer_args(n, layer, false, in, nullptr);
+    a.gout_bf16 = a.out_bf16;  // the output gradient is stored like the layer's output
     double wb = 0.0, wf = 0.0;
     layer_work(a, batch, wb, wf);
     NetTimed tm;
@@ -1349,6 +1538,16 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
             oBA[l] = take((size_t)9 * K2pa * N2pa * 4);
             oBhA[l] = take((size_t)9 * K2pa * N2pa * 2);
         }
+        size_t oS[8] = {0, 0, 0, 0, 0, 0, 0, 0}, oZ = 0;
+        bool any_stack = false;
+        for (int l = 0; l < nlayers; ++l) {
+            n->stacked[l] = n->bf16 && channels[l + 1] == 1 && channels[l] > 1;
+            if (n->stacked[l]) {
+                oS[l] = take((size_t)80 * pad16(8 * channels[l]) * 2);
+                any_stack = true;
+            }
+        }
+        if (any_stack) oZ = take((size_t)max_batch * 2 * c->g.Vh * 9 * 48);
         size_t oA[9];
         int cmax = 1;
         for (int l = 0; l <= nlayers; ++l) {
@@ -1373,6 +1572,8 @@ lqcd_status lqcd_net_create(lqcd_ctx* c, int nlayers, const int* channels, int b
             n->BhA[l] = reinterpret_cast<uint16_t*>(oBhA[l]);
         }
         for (int l = 0; l <= nlayers; ++l) n->act[l] = reinterpret_cast<float*>(oA[l]);
+        for (int l = 0; l < nlayers; ++l) n->BhS[l] = reinterpret_cast<uint16_t*>(oS[l]);
+        n->zbuf = reinterpret_cast<float*>(oZ);
         n->gact[0] = reinterpret_cast<float*>(oG0);
         n->gact[1] = reinterpret_cast<float*>(oG1);
         n->red = reinterpret_cast<double*>(oR);
@@ -1447,6 +1648,13 @@ lqcd_status lqcd_net_set_workspace(lqcd_net* n, void* ptr, size_t bytes)
     fix(n->W); fix(n->gW); fix(n->m1); fix(n->m2);
     for (int l = 0; l < n->nlayers; ++l) { fix(n->Bf[l]); fix(n->Bh[l]); fix(n->BfA[l]); fix(n->BhA[l]); }
     for (int l = 0; l <= n->nlayers; ++l) fix(n->act[l]);
+    bool any_stack = false;
+    for (int l = 0; l < n->nlayers; ++l)
+        if (n->stacked[l]) {
+            fix(n->BhS[l]);
+            any_stack = true;
+        }
+    if (any_stack) fix(n->zbuf);
     fix(n->gact[0]); fix(n->gact[1]); fix(n->red); fix(n->partials); fix(n->tickets);
     n->ws = base;
     n->ws_bytes = bytes;
