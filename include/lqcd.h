@@ -90,9 +90,7 @@ typedef enum {
     LQCD_BF16 = 3,
     LQCD_F16_LINKS = 4,
     LQCD_BF16_LINKS = 5,
-    LQCD_F64_DF = 6,  /* FP64 storage and layout, arithmetic in pairs of FP32
-                         (double-float, ~48-bit significand): FP64-accurate
-                         operator applications at FP32 instruction rate */
+    /* 6 is not used */
     LQCD_F16_SPINORS = 7,   /* FP16 spinors (per-site norm), FP32 links and clover */
     LQCD_BF16_SPINORS = 8,  /* BF16 spinors (per-site norm), FP32 links and clover */
     LQCD_NPREC = 9
@@ -194,11 +192,9 @@ typedef struct {
     int check_interval;      /* host reads the residual every this many iterations */
     int nkrylov;             /* FGCR restart length */
     int use_graph;           /* 1: replay the iteration block as a CUDA graph */
-    int residual_prec;       /* LQCD_F64 (default) or LQCD_F64_DF: arithmetic of the
+    int residual_prec;       /* LQCD_F64 (the only value): arithmetic of the
                                 reliable-update, candidate-check and FGCR restart
-                                residuals of a mixed solve (an FP64 inner solve always
-                                uses LQCD_F64); the final reported residual is always
-                                native FP64 */
+                                residuals of a mixed solve */
     int ndefl;               /* FGMRES-DR: harmonic Ritz vectors kept at a restart
                                 (0 <= ndefl <= 16, < nkrylov; 0: plain restarted FGMRES) */
     int persistent;          /* 1: even-odd CG runs each block of check_interval inner

@@ -129,7 +129,7 @@ lqcd_status launch_dslash(lqcd_ctx* c, const DslashArgs& A0, int P, bool dag, in
     case MODE_BF16_LINKS: e = dslash_dispatch_bf16links(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case MODE_F16_SPINORS: e = dslash_dispatch_f16spinors(A, rc, dag, epi, red, nrhs, block, c->stream); break;
     case MODE_BF16_SPINORS: e = dslash_dispatch_bf16spinors(A, rc, dag, epi, red, nrhs, block, c->stream); break;
-    default: e = dslash_dispatch_df(A, rc, dag, epi, red, nrhs, block, c->stream); break;
+    default: return fail(LQCD_ERR_INVALID, "launch_dslash: bad precision mode");
     }
     LQ_CUDA(e);
     if (timed) {
@@ -421,7 +421,7 @@ lqcd_status lqcd_set_workspace(lqcd_ctx* c, void* ptr, size_t bytes)
 lqcd_status lqcd_field_bytes(const lqcd_ctx* c, lqcd_prec prec, size_t* bytes)
 {
     if (!c || !bytes) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: null argument");
-    if (prec < LQCD_F64 || prec >= LQCD_NPREC) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: bad precision");
+    if (!valid_mode(prec)) return fail(LQCD_ERR_INVALID, "lqcd_field_bytes: bad precision");
     *bytes = c->field_bytes(prec);
     return LQCD_OK;
 }
@@ -487,7 +487,7 @@ lqcd_status lqcd_clover_compute(lqcd_ctx* c, double kappa, double csw)
 
 static lqcd_status check_prec(const lqcd_ctx* c, int prec)
 {
-    if (prec < LQCD_F64 || prec >= LQCD_NPREC) return fail(LQCD_ERR_INVALID, "bad precision");
+    if (!valid_mode(prec)) return fail(LQCD_ERR_INVALID, "bad precision");
     if (!c->holds(mode_pg(prec))) return fail(LQCD_ERR_STATE, "precision not held by this context (cfg.prec_mask)");
     return LQCD_OK;
 }
@@ -771,8 +771,6 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
     p->ndefl = 0;
     p->persistent = 0;
     p->persistent_wait_us = 0;
-    // native FP64: the double-float kernels measured slower on GB300 (255
-    // registers, one 4-warp block per SM, dependent FP32 chains)
     p->residual_prec = LQCD_F64;
     return LQCD_OK;
 }

@@ -363,7 +363,7 @@ lqcd_status clover_apply_launch(lqcd_ctx* c, void* out, const void* in, int pari
     case MODE_BF16_LINKS: clover_apply_kernel<PB16, P32><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
     case MODE_F16_SPINORS: clover_apply_kernel<P32, P16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
     case MODE_BF16_SPINORS: clover_apply_kernel<P32, PB16><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
-    default: clover_apply_kernel<PDF, PDF><<<grid, block, 0, c->stream>>>(c->g, o, i, cl, rb); break;
+    default: return fail(LQCD_ERR_INVALID, "clover apply: bad precision mode");
     }
     LQ_CUDA(cudaGetLastError());
     c->launches++;

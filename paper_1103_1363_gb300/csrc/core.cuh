@@ -18,67 +18,10 @@
 
 namespace lqcd {
 
-// PDF is a template tag only: FP64 storage, double-float arithmetic.
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };
-
-// ---------------------------------------------------------- double-float
-// A value hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2: a ~48-bit
-// significand from FP32 operations (Dekker 1971; Knuth's two-sum).  GB300
-// runs FP64 at a small fraction of its FP32 rate, so FP64-accurate
-// operator applications are cheaper in pairs of FP32.
-struct dfloat {
-    float hi, lo;
-    __host__ __device__ dfloat() {}
-    __host__ __device__ dfloat(float h) : hi(h), lo(0.f) {}
-    __host__ __device__ dfloat(int h) : hi((float)h), lo(0.f) {}
-    __host__ __device__ dfloat(float h, float l) : hi(h), lo(l) {}
-    __host__ __device__ explicit dfloat(double d)
-    {
-        hi = (float)d;
-        lo = (float)(d - (double)hi);
-    }
-    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
-};
-
-// s + e = a + b exactly (Knuth)
-__device__ __forceinline__ dfloat df_two_sum(float a, float b)
-{
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
-    return dfloat(s, e);
-}
-// s + e = a + b exactly when |a| >= |b| (Dekker)
-__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b)
-{
-    const float s = a + b;
-    return dfloat(s, b - (s - a));
-}
-__device__ __forceinline__ dfloat operator+(const dfloat& a, const dfloat& b)
-{
-    dfloat s = df_two_sum(a.hi, b.hi);
-    const dfloat t = df_two_sum(a.lo, b.lo);
-    s = df_fast_two_sum(s.hi, s.lo + t.hi);
-    return df_fast_two_sum(s.hi, s.lo + t.lo);
-}
-__device__ __forceinline__ dfloat operator-(const dfloat& a) { return dfloat(-a.hi, -a.lo); }
-__device__ __forceinline__ dfloat operator-(const dfloat& a, const dfloat& b) { return a + (-b); }
-__device__ __forceinline__ dfloat operator*(const dfloat& a, const dfloat& b)
-{
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);  // exact error of the product
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfloat operator*(int s, const dfloat& b) { return dfloat((float)s) * b; }
-__device__ __forceinline__ dfloat& operator+=(dfloat& a, const dfloat& b) { return a = a + b; }
-__device__ __forceinline__ dfloat& operator-=(dfloat& a, const dfloat& b) { return a = a - b; }
-__device__ __forceinline__ dfloat& operator*=(dfloat& a, const dfloat& b) { return a = a * b; }
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
 
 template <int P> struct RealT { typedef float type; };
 template <> struct RealT<P64> { typedef double type; };
-template <> struct RealT<PDF> { typedef dfloat type; };
 
 // Accumulation precision of the CG vectors r, x for an inner precision P.
 template <int P> struct AccumP { enum { value = (P == P64) ? P64 : P32 }; };
@@ -89,15 +32,14 @@ __host__ __device__ inline int AccumPrec(int P) { return P == P64 ? P64 : P32; }
 // both in the same precision; modes 4 and 5 store links and clover in FP16 /
 // BF16 and every spinor field in FP32.  The arithmetic is FP64 for mode 0
 // and FP32 otherwise.
-// Mode 6 stores everything in FP64 and computes in double-float.
-enum { MODE_F16_LINKS = 4, MODE_BF16_LINKS = 5, MODE_DF = 6, MODE_F16_SPINORS = 7, MODE_BF16_SPINORS = 8,
-       NMODES = 9 };
+// Mode 6 is not used.
+enum { MODE_F16_LINKS = 4, MODE_BF16_LINKS = 5, MODE_F16_SPINORS = 7, MODE_BF16_SPINORS = 8, NMODES = 9 };
+__host__ __device__ inline bool valid_mode(int m) { return m >= 0 && m < NMODES && m != 6; }
 __host__ __device__ inline int mode_pg(int m)
 {
     switch (m) {
     case MODE_F16_LINKS: return P16;
     case MODE_BF16_LINKS: return PB16;
-    case MODE_DF: return P64;
     case MODE_F16_SPINORS:
     case MODE_BF16_SPINORS: return P32;
     default: return m;
@@ -108,7 +50,6 @@ __host__ __device__ inline int mode_ps(int m)
     switch (m) {
     case MODE_F16_LINKS:
     case MODE_BF16_LINKS: return P32;
-    case MODE_DF: return P64;
     case MODE_F16_SPINORS: return P16;
     case MODE_BF16_SPINORS: return PB16;
     default: return m;
@@ -174,27 +115,6 @@ template <> struct SpinorIO<P64> {
         double2* p = static_cast<double2*>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_double2(v[2 * k], v[2 * k + 1]);
-    }
-};
-
-// FP64 storage read into / written from double-float registers.
-template <> struct SpinorIO<PDF> {
-    static constexpr int bytes_per_site = 192;
-    __device__ __forceinline__ static void load(const void* base, int stride, int i, dfloat v[24])
-    {
-        const double2* p = static_cast<const double2*>(base);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            double2 c = __ldg(p + (size_t)k * stride + i);
-            v[2 * k] = dfloat(c.x);
-            v[2 * k + 1] = dfloat(c.y);
-        }
-    }
-    __device__ __forceinline__ static void store(void* base, int stride, int i, const dfloat v[24])
-    {
-        double2* p = static_cast<double2*>(base);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
     }
 };
 
@@ -326,21 +246,6 @@ template <int RECON> struct GaugeIO<P64, RECON> {
     }
 };
 
-template <int RECON> struct GaugeIO<PDF, RECON> {
-    static constexpr int nchunk = RECON == 12 ? 6 : 9;
-    __device__ __forceinline__ static void load(const void* base, int stride, int par, int mu, int i, dfloat u[18])
-    {
-        const double2* p = static_cast<const double2*>(base) + (size_t)((par * 4 + mu) * nchunk) * stride + i;
-#pragma unroll
-        for (int k = 0; k < nchunk; ++k) {
-            double2 c = __ldg(p + (size_t)k * stride);
-            u[2 * k] = dfloat(c.x);
-            u[2 * k + 1] = dfloat(c.y);
-        }
-        if (RECON == 12) reconstruct_row2(u);
-    }
-};
-
 template <> struct GaugeIO<P32, 18> {
     static constexpr int nchunk = 9;
     static constexpr int bytes_per_link = 72;
@@ -465,19 +370,6 @@ template <> struct CloverIO<P64> {
     }
 };
 
-template <> struct CloverIO<PDF> {
-    __device__ __forceinline__ static void load_block(const void* base, int stride, int i, int blk, dfloat c[36])
-    {
-        const double2* p = static_cast<const double2*>(base) + (size_t)(18 * blk) * stride + i;
-#pragma unroll
-        for (int k = 0; k < 18; ++k) {
-            double2 v = __ldg(p + (size_t)k * stride);
-            c[2 * k] = dfloat(v.x);
-            c[2 * k + 1] = dfloat(v.y);
-        }
-    }
-};
-
 template <> struct CloverIO<P32> {
     static constexpr int bytes_per_site = 288;
     __device__ __forceinline__ static void load_block(const void* base, int stride, int i, int blk, float c[36])
@@ -571,7 +463,7 @@ __device__ __forceinline__ void clover_apply_site(const void* base, int stride, 
                                                   typename RealT<P>::type out[24])
 {
     typedef typename RealT<P>::type R;
-    if constexpr (P == P64 || P == P32 || P == PDF) {
+    if constexpr (P == P64 || P == P32) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             R c[36];

@@ -426,7 +426,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i,
 // measured slower: the extra accumulators cost occupancy in a kernel whose
 // neighbour gathers are latency-bound.)
 template <int PG, int PS, int RECON, bool DAG, int EPI, bool RED>
-__global__ void __launch_bounds__(DSLASH_MAX_BLOCK, ((PG == P64 || PG == PDF) ? 1 : LQCD_DSLASH_MINB))
+__global__ void __launch_bounds__(DSLASH_MAX_BLOCK, (PG == P64 ? 1 : LQCD_DSLASH_MINB))
     dslash_kernel(const DslashArgs A)
 {
     const int rhs = (int)(blockIdx.x % (unsigned)A.nrhs);
@@ -497,15 +497,7 @@ cudaError_t dispatch_dslash_p(const DslashArgs& A, int recon, bool dag, int epi,
     LQ_CASE(RC, DG, EPI_XPAY, false)     \
     LQ_CASE(RC, DG, EPI_XPAY, true)      \
     LQ_CASE(RC, DG, EPI_CG, true)
-    if constexpr (PG == PDF) {
-        // FP64-accurate residuals only: no fused CG update
-        LQ_CASE(18, false, EPI_NONE, false)
-        LQ_CASE(18, false, EPI_CLOVINV, false)
-        LQ_CASE(18, false, EPI_XPAY, false)
-        LQ_CASE(18, true, EPI_NONE, false)
-        LQ_CASE(18, true, EPI_CLOVINV, false)
-        LQ_CASE(18, true, EPI_XPAY, false)
-    } else if constexpr (PG == P64) {
+    if constexpr (PG == P64) {
         LQ_EPIS(18, false)
         LQ_EPIS(18, true)
     } else {

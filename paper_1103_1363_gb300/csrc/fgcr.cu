@@ -182,9 +182,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     const int mode = p->inner_prec;
     if (mode_ps(mode) != P32) return fail(LQCD_ERR_INVALID, "lqcd_solve: FGCR runs with FP32 vectors (inner_prec F32, F16_LINKS or BF16_LINKS)");
     const bool log = getenv("LQCD_LOG") != nullptr;
-    if (p->residual_prec != LQCD_F64 && p->residual_prec != LQCD_F64_DF)
-        return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64 or LQCD_F64_DF");
-    const int pres = p->residual_prec;
+    if (p->residual_prec != LQCD_F64) return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64");
     const size_t fb64 = c->field_bytes(P64), rb64 = 2 * fb64;
     const size_t fb = c->field_bytes(P32), fld = 2 * fb;
     char* B = vec64_field(c, 0, 0);
@@ -251,18 +249,11 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         return read(upd, out, 2);
     };
     while (true) {
-        // restart: r = b - M x with FP64 accuracy; stop on the true residual,
-        // confirmed with native FP64 arithmetic when double-float was used
-        LQ_TRY(op_full(c, T1, X, pres, false, 1, rb64));
+        // restart: r = b - M x in FP64; stop on the true residual
+        LQ_TRY(op_full(c, T1, X, P64, false, 1, rb64));
         LQ_TRY(blas_xmy_norm(c, T2, B, T1, P64, 1, rb64, 2, SC_TMP + 2));
         LQ_TRY(read(c->scal, h, SC_PER_RHS));
         res = bn2 > 0 ? std::sqrt(h[SC_TMP + 2] / bn2) : 0.0;
-        if (res <= tol && pres != P64) {
-            LQ_TRY(op_full(c, T1, X, P64, false, 1, rb64));
-            LQ_TRY(blas_xmy_norm(c, T2, B, T1, P64, 1, rb64, 2, SC_TMP + 2));
-            LQ_TRY(read(c->scal, h, SC_PER_RHS));
-            res = bn2 > 0 ? std::sqrt(h[SC_TMP + 2] / bn2) : 0.0;
-        }
         if (log) fprintf(stderr, "[lqcd] fgcr iter %d restart, true residual %.3e\n", iters, res);
         if (!std::isfinite(res)) { status = LQCD_ERR_BREAKDOWN; break; }
         if (res <= tol) break;

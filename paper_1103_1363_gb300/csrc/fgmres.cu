@@ -183,9 +183,7 @@ lqcd_status solve_fgmres_dr(lqcd_ctx* c, lqcd_net* net, double* x, const double*
     const int mode = p->inner_prec;
     if (mode_ps(mode) != P32)
         return fail(LQCD_ERR_INVALID, "lqcd_solve: FGMRES-DR runs with FP32 vectors (inner_prec F32, F16_LINKS or BF16_LINKS)");
-    if (p->residual_prec != LQCD_F64 && p->residual_prec != LQCD_F64_DF)
-        return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64 or LQCD_F64_DF");
-    const int pres = p->residual_prec;
+    if (p->residual_prec != LQCD_F64) return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64");
     const bool log = getenv("LQCD_LOG") != nullptr;
     const size_t fb64 = c->field_bytes(P64), rb64 = 2 * fb64;
     const size_t fb = c->field_bytes(P32), fld = 2 * fb;
@@ -317,16 +315,10 @@ lqcd_status solve_fgmres_dr(lqcd_ctx* c, lqcd_net* net, double* x, const double*
     lqcd_status status = LQCD_OK;
     while (true) {
         // FP64 residual of the current x; convergence on it
-        LQ_TRY(op_full(c, T1, X, pres, false, 1, rb64));
+        LQ_TRY(op_full(c, T1, X, P64, false, 1, rb64));
         LQ_TRY(blas_xmy_norm(c, T2, B, T1, P64, 1, rb64, 2, SC_TMP + 2));
         LQ_TRY(read(c->scal, h, SC_PER_RHS));
         res = bn2 > 0 ? std::sqrt(h[SC_TMP + 2] / bn2) : 0.0;
-        if (res <= tol && pres != P64) {
-            LQ_TRY(op_full(c, T1, X, P64, false, 1, rb64));
-            LQ_TRY(blas_xmy_norm(c, T2, B, T1, P64, 1, rb64, 2, SC_TMP + 2));
-            LQ_TRY(read(c->scal, h, SC_PER_RHS));
-            res = bn2 > 0 ? std::sqrt(h[SC_TMP + 2] / bn2) : 0.0;
-        }
         if (log) fprintf(stderr, "[lqcd] fgmres-dr iter %d restart, true residual %.3e\n", iters, res);
         if (!std::isfinite(res)) { status = LQCD_ERR_BREAKDOWN; break; }
         if (res <= tol) break;

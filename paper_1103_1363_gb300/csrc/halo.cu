@@ -369,7 +369,7 @@ lqcd_status lqcd_norm2(lqcd_ctx* c, const void* field, int parity, lqcd_prec pre
     try {
         if (!c || !field || !out) return fail(LQCD_ERR_INVALID, "lqcd_norm2: null argument");
         if (!c->ws) return fail(LQCD_ERR_NOMEM, "no workspace: call lqcd_set_workspace");
-        if (prec < LQCD_F64 || prec >= LQCD_NPREC || prec == LQCD_F64_DF)
+        if (!valid_mode(prec))
             return fail(LQCD_ERR_INVALID, "lqcd_norm2: bad precision");
         if (parity < -1 || parity > 1) return fail(LQCD_ERR_INVALID, "lqcd_norm2: parity must be -1, 0 or 1");
         if (nrhs < 1 || nrhs > c->cfg.max_nrhs) return fail(LQCD_ERR_INVALID, "lqcd_norm2: need 1 <= nrhs <= max_nrhs");

@@ -77,7 +77,6 @@ cudaError_t dslash_dispatch_f16(const DslashArgs&, int, bool, int, bool, int, in
 cudaError_t dslash_dispatch_bf16(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_f16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_bf16links(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
-cudaError_t dslash_dispatch_df(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_f16spinors(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 cudaError_t dslash_dispatch_bf16spinors(const DslashArgs&, int, bool, int, bool, int, int, cudaStream_t);
 

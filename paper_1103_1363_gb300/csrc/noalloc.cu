@@ -43,7 +43,7 @@ extern "C" lqcd_status lqcd_dslash_schur_static(lqcd_ctx* c, void* out, const vo
     try {
         if (!c) return fail(LQCD_ERR_INVALID, "null context");
         if (!c->ws) return fail(LQCD_ERR_NOMEM, "no workspace: call lqcd_set_workspace");
-        if (prec < LQCD_F64 || prec >= LQCD_NPREC) return fail(LQCD_ERR_INVALID, "bad precision");
+        if (!valid_mode(prec)) return fail(LQCD_ERR_INVALID, "bad precision");
         if (!c->holds(mode_pg(prec))) return fail(LQCD_ERR_STATE, "precision not held by this context");
         if (!out || !in) return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: null field");
         if (out == in) return fail(LQCD_ERR_INVALID, "lqcd_dslash_schur_static: out must not alias in");

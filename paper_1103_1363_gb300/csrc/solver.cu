@@ -38,7 +38,6 @@ struct Cg {
     char *XLO, *RV;                   // accumulation precision full fields (rhs stride rba)
     int nf;                           // 1 (odd parity only) or 2 (full lattice)
     size_t o64, oi, oa;               // byte offset of the solved parity in each field
-    int Pres = P64;                   // mode of the FP64-accurate residuals (P64 or MODE_DF)
     long reliable = 0, checks = 0;
 };
 
@@ -179,10 +178,10 @@ lqcd_status true_system_residual(Cg& s)
 {
     lqcd_ctx* c = s.c;
     if (s.eo) {
-        LQ_TRY(op_schur(c, s.T1 + s.fb64, s.X + s.fb64, s.T2, s.Pres, false, s.R, s.rb64, s.rb64, -1));
+        LQ_TRY(op_schur(c, s.T1 + s.fb64, s.X + s.fb64, s.T2, P64, false, s.R, s.rb64, s.rb64, -1));
         LQ_TRY(blas_xmy_norm(c, s.T2 + s.fb64, s.BH + s.fb64, s.T1 + s.fb64, P64, s.R, s.rb64, 1, SC_TMP + 2));
     } else {
-        LQ_TRY(op_full(c, s.T1, s.X, s.Pres, false, s.R, s.rb64));
+        LQ_TRY(op_full(c, s.T1, s.X, P64, false, s.R, s.rb64));
         LQ_TRY(blas_xmy_norm(c, s.T2, s.B, s.T1, P64, s.R, s.rb64, 2, SC_TMP + 2));
     }
     return LQCD_OK;
@@ -202,7 +201,7 @@ lqcd_status normal_residual_eo(Cg& s, const char* d_odd, int slot)
         LQ_TRY(convert_field(c, d32, P32, d_odd, P64, s.R, s.rba, s.rb64, 1, -1));
         return op_schur(c, s.RV + s.fba, d32, tmp, LQCD_F32, true, s.R, s.rba, s.rba, slot);
     }
-    LQ_TRY(op_schur(c, s.RH + s.fb64, d_odd, s.T1, s.Pres, true, s.R, s.rb64, s.rb64, -1));
+    LQ_TRY(op_schur(c, s.RH + s.fb64, d_odd, s.T1, P64, true, s.R, s.rb64, s.rb64, -1));
     return convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, s.R, s.rba, s.rb64, 1, slot);
 }
 
@@ -217,7 +216,7 @@ lqcd_status reliable_update(Cg& s, int j)
     if (s.eo) {
         LQ_TRY(normal_residual_eo(s, s.T2 + s.fb64, rr_slot(j) + 1));
     } else {
-        LQ_TRY(op_full(c, s.RH, s.T2, s.Pres, true, s.R, s.rb64));
+        LQ_TRY(op_full(c, s.RH, s.T2, P64, true, s.R, s.rb64));
         LQ_TRY(convert_field(c, s.RV, s.PA, s.RH, P64, s.R, s.rba, s.rb64, 1, rr_slot(j)));
         LQ_TRY(convert_field(c, s.RV + s.fba, s.PA, s.RH + s.fb64, P64, s.R, s.rba, s.rb64, 1, rr_slot(j) + 1));
     }
@@ -341,9 +340,7 @@ lqcd_status cg_setup(CgRun& run, lqcd_ctx* c, double* x, const double* b, double
     s.o64 = s.eo ? s.fb64 : 0;
     s.oi = s.eo ? s.fbi : 0;
     s.oa = s.eo ? s.fba : 0;
-    if (p->residual_prec != LQCD_F64 && p->residual_prec != LQCD_F64_DF)
-        return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64 or LQCD_F64_DF");
-    s.Pres = (s.Pi == P64) ? P64 : p->residual_prec;
+    if (p->residual_prec != LQCD_F64) return fail(LQCD_ERR_INVALID, "lqcd_solve: residual_prec must be LQCD_F64");
     const size_t canon_rb = (size_t)c->volume * 192;
     run.host_io = !is_device(b);
     if (run.host_io != !is_device(x)) return fail(LQCD_ERR_INVALID, "lqcd_solve: x and b must both be host or both device");

@@ -28,12 +28,13 @@ _lib = C.CDLL(LIB_PATH)
 LQCD_OK = 0
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_CUDA", 3: "ERR_NOMEM", 4: "ERR_STATE",
           5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_CLOVER_SINGULAR"}
-F64, F32, F16, BF16, F16_LINKS, BF16_LINKS, F64_DF, F16_SPINORS, BF16_SPINORS = range(9)
+F64, F32, F16, BF16, F16_LINKS, BF16_LINKS = range(6)
+F16_SPINORS, BF16_SPINORS = 7, 8  # 6 is not used
 PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "f16links": F16_LINKS,
-        "bf16links": BF16_LINKS, "f64df": F64_DF, "f16spinors": F16_SPINORS, "bf16spinors": BF16_SPINORS}
-PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df", "f16spinors", "bf16spinors")
+        "bf16links": BF16_LINKS, "f16spinors": F16_SPINORS, "bf16spinors": BF16_SPINORS}
+PREC_NAMES = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", None, "f16spinors", "bf16spinors")  # by value
 # storage precision of links / clover for each mode (the bit it needs in prec_mask)
-_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16, F64_DF: F64,
+_STORAGE = {F64: F64, F32: F32, F16: F16, BF16: BF16, F16_LINKS: F16, BF16_LINKS: BF16,
             F16_SPINORS: F32, BF16_SPINORS: F32}
 OP_HOP, OP_SCHUR, OP_FULL, DAG = 0, 1, 2, 1 << 8
 SOLVER_CG_EO, SOLVER_CG_FULL, SOLVER_FGCR, SOLVER_FGMRES_DR = 0, 1, 2, 3
@@ -369,7 +370,7 @@ def lqcd_profile_read(ctx):
     arr = (lqcd_profile_entry * len(PREC_NAMES))()
     _check(_lib.lqcd_profile_read(ctx, arr), "lqcd_profile_read")
     return {PREC_NAMES[i]: {k: getattr(arr[i], k) for k, _ in lqcd_profile_entry._fields_}
-            for i in range(len(PREC_NAMES))}
+            for i in range(len(PREC_NAMES)) if PREC_NAMES[i]}
 
 
 def solver_params(**kw):

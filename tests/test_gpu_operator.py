@@ -17,10 +17,9 @@ from tests.gpu_helpers import (gauge, gpu_apply, hop_ref, parity_mask, rel, requ
 
 pytestmark = pytest.mark.gpu
 
-# f64df: FP64 storage, double-float arithmetic (~48-bit significand)
 TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 3e-3, "bf16": 2e-2, "f16links": 3e-3, "bf16links": 2e-2,
-       "f64df": 1e-12, "f16spinors": 3e-3, "bf16spinors": 2e-2}
-ALL = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f64df", "f16spinors", "bf16spinors")
+       "f16spinors": 3e-3, "bf16spinors": 2e-2}
+ALL = ("f64", "f32", "f16", "bf16", "f16links", "bf16links", "f16spinors", "bf16spinors")
 
 # several tiles with a ragged tail (Vh = 288, 1152+...), the 2^4 degenerate
 # lattice (x+mu = x-mu), and a non-cubic shape
@@ -101,7 +100,7 @@ def test_schur_and_full_operator(lq, dims, kind):
     precs = ("f64", "f32") if dims[3] >= 32 else ALL
     for prec in precs:
         tol = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3, "bf16": 3e-2, "f16links": 5e-3,
-               "bf16links": 3e-2, "f64df": 1e-12, "f16spinors": 5e-3, "bf16spinors": 3e-2}[prec]
+               "bf16links": 3e-2, "f16spinors": 5e-3, "bf16spinors": 3e-2}[prec]
         for dag in (False, True):
             got = gpu_apply(lat, prec, psi, 1, 1, lambda o, i: lat.dslash(
                 o, i, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec))
