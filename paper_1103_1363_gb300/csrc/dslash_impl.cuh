@@ -120,9 +120,47 @@ __device__ __forceinline__ void accumulate(R acc[24], const R w[12])
 // w = U h (ADJ = false) or U^dag h (ADJ = true) for both colour vectors of h.
 // Each real product is its own multiply-add into the running sum (one
 // fused instruction each; a - b*c contracts with the sign folded in).
-template <bool ADJ, class R>
+// PACK (FP32 only): the same products as packed two-lane instructions.
+template <bool ADJ, bool PACK = false, class R>
 __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[12])
 {
+    if constexpr (PACK && sizeof(R) == 4) {
+        // FP32: the two colour vectors share every link entry, so lane s of
+        // a packed pair carries colour vector s through the same sequence of
+        // products (per lane the same roundings as the scalar form below)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 re, im;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int k = ADJ ? 2 * (3 * b + a) : 2 * (3 * a + b);
+                const float2 ur = make_float2(u[k], u[k]);
+                const float2 ui = make_float2(u[k + 1], u[k + 1]);
+                const float2 nui = make_float2(-u[k + 1], -u[k + 1]);
+                const float2 hr = make_float2(h[2 * b], h[2 * (3 + b)]);
+                const float2 hi = make_float2(h[2 * b + 1], h[2 * (3 + b) + 1]);
+                if (b == 0) {
+                    re = __fmul2_rn(ur, hr);
+                    im = __fmul2_rn(ur, hi);
+                } else {
+                    re = __ffma2_rn(ur, hr, re);
+                    im = __ffma2_rn(ur, hi, im);
+                }
+                if (ADJ) {
+                    re = __ffma2_rn(ui, hi, re);
+                    im = __ffma2_rn(nui, hr, im);
+                } else {
+                    re = __ffma2_rn(nui, hi, re);
+                    im = __ffma2_rn(ui, hr, im);
+                }
+            }
+            w[2 * a] = re.x;
+            w[2 * a + 1] = im.x;
+            w[2 * (3 + a)] = re.y;
+            w[2 * (3 + a) + 1] = im.y;
+        }
+        return;
+    }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
@@ -158,7 +196,7 @@ __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[1
 // arithmetic is in RealT<PS> (FP64 only when everything is FP64).
 // HALO (sub-domain interior pass): a hop across the local boundary of a
 // cut direction is left out; it arrives later as a face.
-template <int PG, int PS, int RECON, int MU, bool DAG, bool HALO = false>
+template <int PG, int PS, int RECON, int MU, bool DAG, bool HALO = false, bool PACK = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int i, int full, const int c[4],
                                         int stepmu, typename RealT<PS>::type acc[24])
 {
@@ -178,7 +216,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
             for (int k = 0; k < 12; ++k) h[k] = -h[k];
         }
         GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
-        su3_mul_half<false>(u, h, w);
+        su3_mul_half<false, PACK>(u, h, w);
         accumulate<MU, DAG ? +1 : -1>(acc, w);
     }
     // backward: (1 + g) U_mu(x - mu)^dag in(x - mu)   [dagger: (1 - g)]
@@ -190,7 +228,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
             for (int k = 0; k < 12; ++k) h[k] = -h[k];
         }
         GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
-        su3_mul_half<true>(u, h, w);
+        su3_mul_half<true, PACK>(u, h, w);
         accumulate<MU, DAG ? -1 : +1>(acc, w);
     }
 }
@@ -238,7 +276,7 @@ __device__ __forceinline__ void load_half_hop(const char* in, const void* gauge,
     }
 }
 
-template <int ISBF, int RECON, int MU, bool BWD, bool DAG>
+template <int ISBF, int RECON, int MU, bool BWD, bool DAG, bool PACK>
 __device__ __forceinline__ void compute_half_hop(const HalfHopRaw<RECON>& r, bool flip, float acc[24])
 {
     float v[24], h[12], u[18], w[12];
@@ -263,20 +301,20 @@ __device__ __forceinline__ void compute_half_hop(const HalfHopRaw<RECON>& r, boo
     const float scale = flip ? -r.n : r.n;
 #pragma unroll
     for (int k = 0; k < 12; ++k) h[k] *= scale;
-    su3_mul_half<BWD>(u, h, w);
+    su3_mul_half<BWD, PACK>(u, h, w);
     accumulate<MU, S>(acc, w);
 }
 
-template <int ISBF, int RECON, bool DAG, int H>
+template <int ISBF, int RECON, bool DAG, bool PACK, int H>
 __device__ __forceinline__ void half_pipeline_step(const char* in, const void* gauge, int stride, int par,
                                                    const HopPlan& hp, HalfHopRaw<RECON> (&buf)[2], float acc[24])
 {
     if constexpr (H < 7) load_half_hop<RECON>(in, gauge, stride, par, hp, H + 1, buf[(H + 1) & 1]);
-    compute_half_hop<ISBF, RECON, H / 2, (H & 1) != 0, DAG>(buf[H & 1], (hp.flip >> H) & 1u, acc);
-    if constexpr (H < 7) half_pipeline_step<ISBF, RECON, DAG, H + 1>(in, gauge, stride, par, hp, buf, acc);
+    compute_half_hop<ISBF, RECON, H / 2, (H & 1) != 0, DAG, PACK>(buf[H & 1], (hp.flip >> H) & 1u, acc);
+    if constexpr (H < 7) half_pipeline_step<ISBF, RECON, DAG, PACK, H + 1>(in, gauge, stride, par, hp, buf, acc);
 }
 
-template <int ISBF, int RECON, bool DAG>
+template <int ISBF, int RECON, bool DAG, bool PACK>
 __device__ __forceinline__ void hop_all_half(const DslashArgs& A, const char* in, int i, int full, const int c[4],
                                              float acc[24])
 {
@@ -300,7 +338,7 @@ __device__ __forceinline__ void hop_all_half(const DslashArgs& A, const char* in
     }
     HalfHopRaw<RECON> buf[2];
     load_half_hop<RECON>(in, A.gauge, A.g.stride, A.par, hp, 0, buf[0]);
-    half_pipeline_step<ISBF, RECON, DAG, 0>(in, A.gauge, A.g.stride, A.par, hp, buf, acc);
+    half_pipeline_step<ISBF, RECON, DAG, PACK, 0>(in, A.gauge, A.g.stride, A.par, hp, buf, acc);
 }
 
 // Threads per block are at most DSLASH_MAX_BLOCK; DSLASH_MIN_BLOCKS resident
@@ -403,14 +441,17 @@ __device__ __forceinline__ void dslash_site(const DslashArgs& A, int rhs, int i,
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
+    // packed link products in the launches that neither reduce nor update
+    // (measured faster there; slower in the reducing launches of the solver)
+    constexpr bool PACK = !(RED || EPI == EPI_CG);
     if constexpr ((PS == P16 || PS == PB16) && PG == PS) {
         static_assert(!HALO, "sub-domain hops use the generic gather");
-        hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG>(A, in, i, full, c, acc);
+        hop_all_half<PS == PB16 ? 1 : 0, RECON, DAG, PACK>(A, in, i, full, c, acc);
     } else {
-        hop_dir<PG, PS, RECON, 0, DAG, HALO>(A, in, i, full, c, 1, acc);
-        hop_dir<PG, PS, RECON, 1, DAG, HALO>(A, in, i, full, c, A.g.L[0], acc);
-        hop_dir<PG, PS, RECON, 2, DAG, HALO>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
-        hop_dir<PG, PS, RECON, 3, DAG, HALO>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
+        hop_dir<PG, PS, RECON, 0, DAG, HALO, PACK>(A, in, i, full, c, 1, acc);
+        hop_dir<PG, PS, RECON, 1, DAG, HALO, PACK>(A, in, i, full, c, A.g.L[0], acc);
+        hop_dir<PG, PS, RECON, 2, DAG, HALO, PACK>(A, in, i, full, c, A.g.L[0] * A.g.L[1], acc);
+        hop_dir<PG, PS, RECON, 3, DAG, HALO, PACK>(A, in, i, full, c, A.g.L[0] * A.g.L[1] * A.g.L[2], acc);
     }
     if (HALO && on_cut_face(A.g, c)) {
         SpinorIO<PS>::store(static_cast<char*>(A.out) + rhs * A.out_rb, A.g.stride, i, acc);

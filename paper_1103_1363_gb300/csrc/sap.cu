@@ -107,7 +107,7 @@ __device__ __forceinline__ void sap_hop(const SapArgs& a, const float4* rs, cons
         smem_load(rs, a.vol, l + lstride, v);
         project<MU, -1>(v, h);
         GaugeIO<P32, RECON>::load(a.gauge, a.g.stride, s.par, MU, s.cb, u);
-        su3_mul_half<false>(u, h, w);
+        su3_mul_half<false, true>(u, h, w);
         accumulate<MU, -1>(acc, w);
     }
     if (s.l[MU] > 0) {
@@ -116,7 +116,7 @@ __device__ __forceinline__ void sap_hop(const SapArgs& a, const float4* rs, cons
         smem_load(rs, a.vol, l - lstride, v);
         project<MU, +1>(v, h);
         GaugeIO<P32, RECON>::load(a.gauge, a.g.stride, 1 - s.par, MU, full_index(a.g, cc) >> 1, u);
-        su3_mul_half<true>(u, h, w);
+        su3_mul_half<true, true>(u, h, w);
         accumulate<MU, +1>(acc, w);
     }
 }
@@ -178,14 +178,14 @@ __device__ __forceinline__ void sap_hop_staged(const SapArgs& a, const float4* r
         smem_load(rs, a.vol, l + lstride, v);
         project<MU, -1>(v, h);
         SmemLinks<RECON>::load(lk, a.vol, MU, l, u);
-        su3_mul_half<false>(u, h, w);
+        su3_mul_half<false, true>(u, h, w);
         accumulate<MU, -1>(acc, w);
     }
     if (s.l[MU] > 0) {
         smem_load(rs, a.vol, l - lstride, v);
         project<MU, +1>(v, h);
         SmemLinks<RECON>::load(lk, a.vol, MU, l - lstride, u);
-        su3_mul_half<true>(u, h, w);
+        su3_mul_half<true, true>(u, h, w);
         accumulate<MU, +1>(acc, w);
     }
 }
@@ -209,7 +209,7 @@ __device__ __forceinline__ void sap_border_hop(const SapArgs& a, const SapSite& 
             for (int k = 0; k < 12; ++k) h[k] = -h[k];
         }
         GaugeIO<P32, RECON>::load(a.gauge, a.g.stride, s.par, MU, s.cb, u);
-        su3_mul_half<false>(u, h, w);
+        su3_mul_half<false, true>(u, h, w);
         accumulate<MU, -1>(acc, w);
     }
     if (s.l[MU] == 0) {
@@ -223,7 +223,7 @@ __device__ __forceinline__ void sap_border_hop(const SapArgs& a, const SapSite& 
             for (int k = 0; k < 12; ++k) h[k] = -h[k];
         }
         GaugeIO<P32, RECON>::load(a.gauge, a.g.stride, 1 - s.par, MU, cbn, u);
-        su3_mul_half<true>(u, h, w);
+        su3_mul_half<true, true>(u, h, w);
         accumulate<MU, +1>(acc, w);
     }
 }
