@@ -5,8 +5,9 @@ Workload (synthetic, seeded): 32^3 x 64 lattice, links exp(i 0.4 H) (gauge
 seed 3), kappa 0.1355, csw 1.0 (four-leaf clover), Gaussian source (seed 0),
 antiperiodic t; mixed-precision even-odd CG on the normal equations: FP16
 spinor storage with per-site norms, FP32 links (recon-12) and clover, FP32
-arithmetic inside, FP64 reliable update every 50 iterations, stopped at true
-residual |b - M x|/|b| <= 1e-10.  (With the links and clover in FP16 too the
+arithmetic inside, FP64 reliable update whenever the iterated residual has
+fallen by 10 since the last one (and at least every 100 iterations), stopped
+at true residual |b - M x|/|b| <= 1e-10.  (With the links and clover in FP16 too the
 operator's rounding, amplified by the condition number of the normal
 equations, triples the iteration count; that variant is timed as well.)
 
@@ -47,12 +48,17 @@ WORKLOADS = {
     "24c48": dict(dims=(24, 24, 24, 48), eps=0.4, gauge_seed=3, src_seed=0, kappa=0.1355, csw=1.0),
 }
 TOL = 1e-10
+# FP64 residual replacement: every RELIABLE_EVERY iterations or when |r| has
+# fallen below RELIABLE_DELTA times its largest value since the last one
+# (measured at 32^3x64, FP16 spinors: 100 / 0.1 took 380 iterations and 7
+# replacements in 290 ms; 50 / 0.1 took 390 and 9 in 306 ms)
+RELIABLE_EVERY, RELIABLE_DELTA = 100, 0.1
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per output site of the inner hopping kernels,
 # from one ncu capture of a CG iteration on 24^3x48 (the four launches of an
 # iteration: Mhat sweeps with A^-1 and x-pay + norm epilogues, Mhat^dag sweeps
 # with A^-1 and the fused CG update); traffic grows with the sites processed.
-DRAM_BYTES_PER_SITE = {"f16spinors": (766.4 + 820.0 + 766.4 + 1150.9) / 4}
+DRAM_BYTES_PER_SITE = {"f16spinors": (765.3 + 820.3 + 765.6 + 1151.4) / 4}
 STORAGE = {
     "f32": "f32 spinors, links (recon-12) and clover",
     "f16": "f16 spinors (per-site norm), links (recon-12) and clover",
@@ -178,7 +184,8 @@ def run_ours(args, w, rank, world, local_rank):
     # block sizes (plain, plain reducing, dagger, dagger reducing)
     tuned = {p: lqcd.lqcd_tune(lat.ctx, p) for p in ("f64", args.inner)}
     del Ud
-    params = dict(inner_prec=args.inner, reliable_interval=50, check_interval=10)
+    params = dict(inner_prec=args.inner, reliable_interval=RELIABLE_EVERY, reliable_delta=RELIABLE_DELTA,
+                  check_interval=10)
 
     def barrier():
         if world > 1:
@@ -340,7 +347,7 @@ def multi_rhs_leg(dev):
     b = torch.from_numpy(srcs).to(dev)
     x = torch.zeros_like(b)
     res = {"workload": "12 point sources, 24x24x24x48, exp(i 0.5 H) links, kappa 0.135, csw 1.0, tol 1e-10"}
-    mixed = dict(reliable_interval=50, check_interval=10, use_graph=1)
+    mixed = dict(reliable_interval=RELIABLE_EVERY, reliable_delta=RELIABLE_DELTA, check_interval=10, use_graph=1)
 
     def summary(t, sts):
         return {"seconds": round(t, 4), "iterations_max": max(s["iterations"] for s in sts),
@@ -870,7 +877,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "storage": STORAGE[args.inner] + "; f64 reliable updates",
             "data": "synthetic",
-            "config": {"workload": workload_name(w), "inner": args.inner, "reliable_update_every": 50,
+            "config": {"workload": workload_name(w), "inner": args.inner, "reliable_update_every": RELIABLE_EVERY,
+                       "reliable_delta": RELIABLE_DELTA,
                        "recon": 12, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set > 1 GB per solve)"},
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r.get("e2e"),
