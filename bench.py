@@ -483,6 +483,8 @@ def run_hop_kernel(args, w):
     hb, src = measured_peaks()
     lat = lqcd.Lattice(dims, precisions=("f64", "f32", args.prec), recon=args.recon, stream=stream)
     lat.gauge_load(U)
+    if args.staged:  # the shared-memory staged kernel for the plain launches
+        lqcd.lqcd_tune_set(lat.ctx, args.prec, (lqcd.BLOCK_STAGED, 128, lqcd.BLOCK_STAGED, 128))
     with torch.cuda.stream(stream):
         fins = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
         fouts = [lat.new_field(args.prec, nrhs=R) for _ in range(nbuf)]
@@ -502,7 +504,8 @@ def run_hop_kernel(args, w):
     sb = spinor[args.prec]
     lb = link[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
     comp = (2 * sb * R + 8 * lb) * Vh
-    print(json.dumps({"kernel": "hop", "prec": args.prec, "recon": args.recon, "nrhs": R,
+    print(json.dumps({"kernel": "hop", "variant": "staged" if args.staged else "gather", "prec": args.prec,
+                      "recon": args.recon, "nrhs": R,
                       "workload": workload_name(w),
                       "us_per_launch": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / R, 2),
                       "gflops": round(1320.0 * Vh * R / t / 1e9, 1),
@@ -839,6 +842,8 @@ def main():
     ap.add_argument("--prec", default="f16", help="precision of --kernel hop")
     ap.add_argument("--recon", type=int, default=12, choices=[12, 18], help="link storage of --kernel hop")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per launch of --kernel hop")
+    ap.add_argument("--staged", action="store_true",
+                    help="--kernel hop: the shared-memory staged kernel (FP32 links, recon-12) instead of the gathering one")
     ap.add_argument("--cpu-applications", type=int, default=3)
     ap.add_argument("--skip-learned", action="store_true", help="leave out the learned-preconditioner leg")
     args = ap.parse_args()

@@ -465,7 +465,11 @@ lqcd_status lqcd_sync(lqcd_ctx* ctx);
  * x-pay epilogue as in the solvers, with and without the fused norm
  * reduction) at 128, 96, 64 and 32 threads per block on this context's
  * lattice and keep, for each of the four classes, the fastest (a smaller
- * block must win by 2 %) for every later launch of that class.  Reducing
+ * block must win by 2 %) for every later launch of that class.  For the
+ * plain classes of the modes with FP32 links (LQCD_F32, LQCD_F16_SPINORS,
+ * LQCD_BF16_SPINORS) with recon-12 the candidates also include the
+ * shared-memory staged kernel (LQCD_BLOCK_STAGED below), which must win by
+ * 2 % as well.  Reducing
  * launches (fused norms, fused CG updates) write one partial sum per block:
  * they are tuned apart from the plain ones, and for them also the sites each
  * thread handles (one wave of resident blocks, the default, or 1, 4 or 16
@@ -475,6 +479,25 @@ lqcd_status lqcd_sync(lqcd_ctx* ctx);
  * NULL) the sites per thread of the reducing launches [dag] (0: one wave).
  * Synchronises the stream. */
 lqcd_status lqcd_tune(lqcd_ctx* ctx, lqcd_prec prec, int best_block[4], int best_sites[2]);
+
+/* The "block size" that selects the shared-memory staged hopping kernel for
+ * a plain class: each block copies the input spinors of a tile of 4 x 2 x 2
+ * (y, z, t) rows of all Lx/2 checkerboard sites, and of the tile's six faces,
+ * into shared memory with asynchronous copies, then reads every neighbour
+ * from there (the neighbour faces of Sec. 5's kernel, staged on chip).  It
+ * applies to plain launches with FP32 recon-12 links on an uncut lattice with
+ * Lx <= 32, Ly % 4 = Lz % 2 = Lt % 2 = 0; other launches of the class use the
+ * gathering kernel at 128 threads.  Its arithmetic is that of the gathering
+ * kernel, in the same order (the results are identical). */
+#define LQCD_BLOCK_STAGED 1
+
+/* Set the tuner's choices for precision `prec` directly (e.g. ones saved
+ * from an earlier lqcd_tune): block[2 * dag + reducing] in {32, 64, 96, 128}
+ * or, for the plain classes (indices 0 and 2), LQCD_BLOCK_STAGED; sites[dag]
+ * (may be NULL: unchanged) the sites per thread of the reducing launches, 0
+ * (one wave of resident blocks) or 1 to 64.  Anything else is
+ * LQCD_ERR_INVALID and changes nothing.  No GPU work. */
+lqcd_status lqcd_tune_set(lqcd_ctx* ctx, lqcd_prec prec, const int block[4], const int sites[2]);
 
 /* Kernel timing.  While enabled, every hopping-term launch the context
  * issues is bracketed by CUDA events on its stream (graph replays are not

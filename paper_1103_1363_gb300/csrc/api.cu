@@ -706,7 +706,9 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_s
             if (st == LQCD_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
         }
     };
-    const int cands[4] = {128, 96, 64, 32};  // the default first: it wins ties
+    const int cands[5] = {128, 96, 64, 32, DSLASH_STAGED};  // the default first: it wins ties
+    // the staged kernel competes in the plain classes where it applies
+    const bool staged_ok = mode_pg(prec) == P32 && c->recon_of(P32) == 12 && staged_supported(c->g);
     const int spts[4] = {0, 1, 4, 16};       // sites per thread of reducing launches (0: one wave of blocks)
     // reducing launches (fused norms, fused CG updates) write one partial sum
     // per block, so they are tuned apart from the plain ones, and for them
@@ -716,7 +718,8 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_s
             float best = 1e30f;
             int best_b = c->block;
             if (red) c->tuned_spt[prec][dag] = 0;
-            for (int ci = 0; ci < 4 && st == LQCD_OK; ++ci) {
+            for (int ci = 0; ci < 5 && st == LQCD_OK; ++ci) {
+                if (ci == 4 && (red || !staged_ok)) break;
                 c->tuned_block[prec][dag][red] = cands[ci];
                 float ms = 0.f;
                 time_launches(dag, red, ms);
@@ -746,6 +749,32 @@ lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_s
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+    LQ_GUARD_END
+}
+
+static_assert(DSLASH_STAGED == LQCD_BLOCK_STAGED, "the staged kernel's block-size code is part of the ABI");
+
+lqcd_status lqcd_tune_set(lqcd_ctx* c, lqcd_prec prec, const int block[4], const int sites[2])
+{
+    LQ_GUARD_BEGIN
+    LQ_TRY(check_ready(c));
+    LQ_TRY(check_prec(c, prec));
+    if (!block) return fail(LQCD_ERR_INVALID, "lqcd_tune_set: null block");
+    for (int k = 0; k < 4; ++k) {
+        const int b = block[k];
+        const bool plain = (k & 1) == 0;
+        if (!(b == 32 || b == 64 || b == 96 || b == 128 || (plain && b == DSLASH_STAGED)))
+            return fail(LQCD_ERR_INVALID, "lqcd_tune_set: block must be 32, 64, 96, 128 or (plain classes) "
+                                          "LQCD_BLOCK_STAGED");
+    }
+    if (sites)
+        for (int d = 0; d < 2; ++d)
+            if (sites[d] < 0 || sites[d] > 64) return fail(LQCD_ERR_INVALID, "lqcd_tune_set: sites per thread out of range");
+    for (int dag = 0; dag < 2; ++dag)
+        for (int red = 0; red < 2; ++red) c->tuned_block[prec][dag][red] = block[2 * dag + red];
+    if (sites)
+        for (int d = 0; d < 2; ++d) c->tuned_spt[prec][d] = sites[d];
+    return LQCD_OK;
     LQ_GUARD_END
 }
 

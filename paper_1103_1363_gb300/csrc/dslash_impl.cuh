@@ -192,6 +192,25 @@ __device__ __forceinline__ void su3_mul_half(const R u[18], const R h[12], R w[1
     }
 }
 
+// One hop of the sum for the neighbour spinor v: forward (BWD false)
+// (1 - g_mu) U_mu(x) v, backward (1 + g_mu) U_mu(x - mu)^dag v (projectors
+// swapped by DAG); the link is U_mu at checkerboard index lidx of parity
+// lpar; flip: the hop crosses the antiperiodic t boundary.
+template <int PG, int RECON, int MU, bool DAG, bool BWD, bool PACK, class R>
+__device__ __forceinline__ void hop_term(const DslashArgs& A, const R v[24], bool flip, int lpar, int lidx, R acc[24])
+{
+    constexpr int S = (BWD != DAG) ? +1 : -1;
+    R h[12], u[18], w[12];
+    project<MU, S>(v, h);
+    if (flip) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) h[k] = -h[k];
+    }
+    GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, lpar, MU, lidx, u);
+    su3_mul_half<BWD, PACK>(u, h, w);
+    accumulate<MU, S>(acc, w);
+}
+
 // PG: storage of links and clover; PS: storage of spinor fields; the
 // arithmetic is in RealT<PS> (FP64 only when everything is FP64).
 // HALO (sub-domain interior pass): a hop across the local boundary of a
@@ -206,30 +225,14 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const char* in, int
     const int bwd = (c[MU] == 0) ? full + (L - 1) * stepmu : full - stepmu;
     const bool tb = (MU == 3) && A.g.tanti;
     const bool cut = HALO && ((A.g.part >> MU) & 1);
-    R v[24], h[12], u[18], w[12];
-    // forward: (1 - g) U_mu(x) in(x + mu)   [dagger: (1 + g)]
+    R v[24];
     if (!(cut && c[MU] == L - 1)) {
         SpinorIO<PS>::load(in, A.g.stride, fwd >> 1, v);
-        project<MU, DAG ? +1 : -1>(v, h);
-        if (tb && c[3] == L - 1) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) h[k] = -h[k];
-        }
-        GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, A.par, MU, i, u);
-        su3_mul_half<false, PACK>(u, h, w);
-        accumulate<MU, DAG ? +1 : -1>(acc, w);
+        hop_term<PG, RECON, MU, DAG, false, PACK>(A, v, tb && c[3] == L - 1, A.par, i, acc);
     }
-    // backward: (1 + g) U_mu(x - mu)^dag in(x - mu)   [dagger: (1 - g)]
     if (!(cut && c[MU] == 0)) {
         SpinorIO<PS>::load(in, A.g.stride, bwd >> 1, v);
-        project<MU, DAG ? -1 : +1>(v, h);
-        if (tb && c[3] == 0) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) h[k] = -h[k];
-        }
-        GaugeIO<PG, RECON>::load(A.gauge, A.g.stride, 1 - A.par, MU, bwd >> 1, u);
-        su3_mul_half<true, PACK>(u, h, w);
-        accumulate<MU, DAG ? -1 : +1>(acc, w);
+        hop_term<PG, RECON, MU, DAG, true, PACK>(A, v, tb && c[3] == 0, 1 - A.par, bwd >> 1, acc);
     }
 }
 
@@ -348,6 +351,7 @@ __device__ __forceinline__ void hop_all_half(const DslashArgs& A, const char* in
 #define LQCD_DSLASH_MINB 4  // <= 128 registers; 4, 5, 6 measured within 5% on 32^3x64
 #endif
 #define DSLASH_MAX_BLOCK 128
+#define DSLASH_STAGED 1  // a "block size" that selects the shared-memory staged kernel (LQCD_BLOCK_STAGED)
 // Epilogue at output site i of right-hand side rhs for the hopping term
 // acc; nrm accumulates |out|^2 (|r|^2 for EPI_CG).
 template <int PG, int PS, bool DAG, int EPI, bool RED>
@@ -524,11 +528,253 @@ cudaError_t launch_dslash_t(const DslashArgs& A, int nrhs, int block, cudaStream
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staged hop (plain launches, FP32 links): a block takes a
+// tile of STG_TY x STG_TZ x STG_TT rows (y, z, t) of all Lx/2 checkerboard
+// sites, one site per thread, and first copies the input spinors of the
+// tile and of its six faces (the rows one step outside in y, z and t) into
+// shared memory with asynchronous 16-byte copies, which hold no registers
+// while in flight; every neighbour is then read from shared memory (x
+// neighbours lie in the site's own row).  Faces are copied from the
+// periodically wrapped rows.  Rows of the staging buffer: the tile's
+// interior r = (tl TZ + zl) TY + yl, then y-, y+ (index tl TZ + zl), z-, z+
+// (tl TY + yl), t-, t+ (zl TY + yl).
+enum {
+    STG_TY = 4, STG_TZ = 2, STG_TT = 2, STG_NIN = STG_TY * STG_TZ * STG_TT,
+    STG_FY = STG_TZ * STG_TT, STG_FZ = STG_TY * STG_TT, STG_FT = STG_TY * STG_TZ,
+    STG_NROW = STG_NIN + 2 * (STG_FY + STG_FZ + STG_FT), STG_MAXLXH = 16
+};
+
+__host__ __device__ inline bool staged_supported(const Geom& g)
+{
+    return g.part == 0 && g.Lxh <= STG_MAXLXH && g.L[1] % STG_TY == 0 && g.L[2] % STG_TZ == 0 &&
+           g.L[3] % STG_TT == 0;
+}
+
+// Bytes of the staging buffer for spinor storage PS and Lx/2 = lxh.
+__host__ __device__ inline size_t staged_smem_bytes(int PS, int lxh)
+{
+    const size_t ns = (size_t)STG_NROW * lxh;
+    return PS == P32 ? ns * 96 : ns * 52;
+}
+
+// Checkerboard row index ((t Lz + z) Ly + y) of staging row r of the tile
+// with origin (y0, z0, t0).
+__device__ __forceinline__ int stg_row_global(const Geom& g, int r, int y0, int z0, int t0)
+{
+    int yl, zl, tl;
+    if (r < STG_NIN) {
+        yl = r % STG_TY;
+        zl = (r / STG_TY) % STG_TZ;
+        tl = r / (STG_TY * STG_TZ);
+    } else if (r < STG_NIN + 2 * STG_FY) {
+        const int q = r - STG_NIN, f = q % STG_FY;
+        yl = q < STG_FY ? -1 : STG_TY;
+        zl = f % STG_TZ;
+        tl = f / STG_TZ;
+    } else if (r < STG_NIN + 2 * (STG_FY + STG_FZ)) {
+        const int q = r - STG_NIN - 2 * STG_FY, f = q % STG_FZ;
+        zl = q < STG_FZ ? -1 : STG_TZ;
+        yl = f % STG_TY;
+        tl = f / STG_TY;
+    } else {
+        const int q = r - STG_NIN - 2 * (STG_FY + STG_FZ), f = q % STG_FT;
+        tl = q < STG_FT ? -1 : STG_TT;
+        yl = f % STG_TY;
+        zl = f / STG_TY;
+    }
+    int y = y0 + yl, z = z0 + zl, t = t0 + tl;
+    y = y < 0 ? y + g.L[1] : (y >= g.L[1] ? y - g.L[1] : y);
+    z = z < 0 ? z + g.L[2] : (z >= g.L[2] ? z - g.L[2] : z);
+    t = t < 0 ? t + g.L[3] : (t >= g.L[3] ? t - g.L[3] : t);
+    return (t * g.L[2] + z) * g.L[1] + y;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// A staged spinor (row-major staging rows, the field's chunk order).
+template <int PS> struct SpinorSmem;
+template <> struct SpinorSmem<P32> {
+    __device__ __forceinline__ static void load(const unsigned char* sm, int ns, int j, float v[24])
+    {
+        const float4* p = reinterpret_cast<const float4*>(sm);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 c = p[k * ns + j];
+            v[4 * k] = c.x;
+            v[4 * k + 1] = c.y;
+            v[4 * k + 2] = c.z;
+            v[4 * k + 3] = c.w;
+        }
+    }
+};
+template <int ISBF> struct SpinorSmemHalf {
+    __device__ __forceinline__ static void load(const unsigned char* sm, int ns, int j, float v[24])
+    {
+        const uint4* p = reinterpret_cast<const uint4*>(sm);
+        const float n = reinterpret_cast<const float*>(p + 3 * ns)[j];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 c = p[k * ns + j];
+            const float2 a = h2f(c.x, ISBF), b = h2f(c.y, ISBF), d = h2f(c.z, ISBF), e = h2f(c.w, ISBF);
+            v[8 * k + 0] = a.x * n; v[8 * k + 1] = a.y * n;
+            v[8 * k + 2] = b.x * n; v[8 * k + 3] = b.y * n;
+            v[8 * k + 4] = d.x * n; v[8 * k + 5] = d.y * n;
+            v[8 * k + 6] = e.x * n; v[8 * k + 7] = e.y * n;
+        }
+    }
+};
+template <> struct SpinorSmem<P16> : SpinorSmemHalf<0> {};
+template <> struct SpinorSmem<PB16> : SpinorSmemHalf<1> {};
+
+// One hop direction of the staged kernel: the neighbours' staging indices
+// jf, jb, the backward link's checkerboard index bwd_cb.
+template <int PG, int PS, int RECON, int MU, bool DAG>
+__device__ __forceinline__ void hop_dir_staged(const DslashArgs& A, const unsigned char* sm, int ns, int i, int jf,
+                                               int jb, int bwd_cb, bool flipf, bool flipb, float acc[24])
+{
+    float v[24];
+    SpinorSmem<PS>::load(sm, ns, jf, v);
+    hop_term<PG, RECON, MU, DAG, false, true>(A, v, flipf, A.par, i, acc);
+    SpinorSmem<PS>::load(sm, ns, jb, v);
+    hop_term<PG, RECON, MU, DAG, true, true>(A, v, flipb, 1 - A.par, bwd_cb, acc);
+}
+
+// Block b: right-hand side b % nrhs, tile b / nrhs (y fastest, then z, t);
+// blockDim = STG_NIN * Lx/2.  Same arithmetic, in the same order, as the
+// gathering kernel's plain launches.
+template <int PG, int PS, int RECON, bool DAG, int EPI>
+__global__ void __launch_bounds__(STG_NIN * STG_MAXLXH, 2) dslash_staged_kernel(const DslashArgs A)
+{
+    extern __shared__ __align__(16) unsigned char stg_smem[];
+    const Geom& g = A.g;
+    const int rhs = (int)(blockIdx.x % (unsigned)A.nrhs);
+    if (A.skip && A.skip[rhs]) return;  // uniform over the block
+    const int tile = (int)(blockIdx.x / (unsigned)A.nrhs);
+    const int nty = g.L[1] / STG_TY, ntz = g.L[2] / STG_TZ;
+    const int y0 = (tile % nty) * STG_TY, z0 = ((tile / nty) % ntz) * STG_TZ, t0 = (tile / (nty * ntz)) * STG_TT;
+    const int lxh = g.Lxh, ns = STG_NROW * lxh;
+    const int xh = threadIdx.x % lxh, rl = threadIdx.x / lxh;  // this thread's site in the tile
+    const char* in = static_cast<const char*>(A.in) + rhs * A.in_rb;
+
+    // stage: thread (rl, xh) copies column xh of rows rl, rl + NIN, ... of every chunk
+    constexpr int NCH = PS == P32 ? 6 : 3;
+    for (int q = rl; q < NCH * STG_NROW; q += STG_NIN) {
+        const int k = q / STG_NROW, r = q - k * STG_NROW;
+        const int gi = stg_row_global(g, r, y0, z0, t0) * lxh + xh;
+        cp_async16(stg_smem + ((size_t)k * ns + r * lxh + xh) * 16, in + ((size_t)k * g.stride + gi) * 16);
+    }
+    if constexpr (PS != P32) {  // the per-site norms
+        for (int r = rl; r < STG_NROW; r += STG_NIN) {
+            const int gi = stg_row_global(g, r, y0, z0, t0) * lxh + xh;
+            cp_async4(stg_smem + (size_t)3 * ns * 16 + (size_t)(r * lxh + xh) * 4,
+                      in + (size_t)3 * g.stride * 16 + (size_t)gi * 4);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+
+    const int yl = rl % STG_TY, zl = (rl / STG_TY) % STG_TZ, tl = rl / (STG_TY * STG_TZ);
+    int c[4];
+    c[1] = y0 + yl;
+    c[2] = z0 + zl;
+    c[3] = t0 + tl;
+    c[0] = 2 * xh + ((c[1] + c[2] + c[3] + A.par) & 1);
+    const int i = ((c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * lxh + xh;
+    const int full = full_index(g, c);
+    const int row = rl * lxh;
+    float acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0.f;
+    // staging indices of the eight neighbours and checkerboard indices of the backward links
+    {
+        const int xf = c[0] == g.L[0] - 1 ? 0 : c[0] + 1, xb = c[0] == 0 ? g.L[0] - 1 : c[0] - 1;
+        const int bwd = c[0] == 0 ? full + (g.L[0] - 1) : full - 1;
+        hop_dir_staged<PG, PS, RECON, 0, DAG>(A, stg_smem, ns, i, row + (xf >> 1), row + (xb >> 1), bwd >> 1, false,
+                                              false, acc);
+    }
+    {
+        const int s1 = g.L[0];
+        const int jf = (yl + 1 < STG_TY ? rl + 1 : STG_NIN + STG_FY + tl * STG_TZ + zl) * lxh + xh;
+        const int jb = (yl > 0 ? rl - 1 : STG_NIN + tl * STG_TZ + zl) * lxh + xh;
+        const int bwd = c[1] == 0 ? full + (g.L[1] - 1) * s1 : full - s1;
+        hop_dir_staged<PG, PS, RECON, 1, DAG>(A, stg_smem, ns, i, jf, jb, bwd >> 1, false, false, acc);
+    }
+    {
+        const int s2 = g.L[0] * g.L[1];
+        constexpr int bz = STG_NIN + 2 * STG_FY;
+        const int jf = (zl + 1 < STG_TZ ? rl + STG_TY : bz + STG_FZ + tl * STG_TY + yl) * lxh + xh;
+        const int jb = (zl > 0 ? rl - STG_TY : bz + tl * STG_TY + yl) * lxh + xh;
+        const int bwd = c[2] == 0 ? full + (g.L[2] - 1) * s2 : full - s2;
+        hop_dir_staged<PG, PS, RECON, 2, DAG>(A, stg_smem, ns, i, jf, jb, bwd >> 1, false, false, acc);
+    }
+    {
+        const int s3 = g.L[0] * g.L[1] * g.L[2];
+        constexpr int bt = STG_NIN + 2 * (STG_FY + STG_FZ);
+        const int jf = (tl + 1 < STG_TT ? rl + STG_TY * STG_TZ : bt + STG_FT + zl * STG_TY + yl) * lxh + xh;
+        const int jb = (tl > 0 ? rl - STG_TY * STG_TZ : bt + zl * STG_TY + yl) * lxh + xh;
+        const int bwd = c[3] == 0 ? full + (g.L[3] - 1) * s3 : full - s3;
+        const bool tb = g.tanti != 0;
+        hop_dir_staged<PG, PS, RECON, 3, DAG>(A, stg_smem, ns, i, jf, jb, bwd >> 1, tb && c[3] == g.L[3] - 1,
+                                              tb && c[3] == 0, acc);
+    }
+    double nrm = 0.0;
+    dslash_epilogue<PG, PS, DAG, EPI, false>(A, rhs, i, acc, nrm);
+}
+
+template <int PG, int PS, int RECON, bool DAG, int EPI>
+cudaError_t launch_staged_t(const DslashArgs& A, int nrhs, cudaStream_t s)
+{
+    static bool attr = false;  // the largest buffer (Lx/2 = 16) is allowed once per instantiation
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(dslash_staged_kernel<PG, PS, RECON, DAG, EPI>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)staged_smem_bytes(PS, STG_MAXLXH));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long tiles = (long)(A.g.L[1] / STG_TY) * (A.g.L[2] / STG_TZ) * (A.g.L[3] / STG_TT);
+    if (tiles * nrhs > 0x7fffffffL) return cudaErrorInvalidConfiguration;
+    DslashArgs Ar = A;
+    Ar.nrhs = nrhs;
+    dslash_staged_kernel<PG, PS, RECON, DAG, EPI>
+        <<<(unsigned)(tiles * nrhs), STG_NIN * A.g.Lxh, staged_smem_bytes(PS, A.g.Lxh), s>>>(Ar);
+    return cudaGetLastError();
+}
+
 // Runtime dispatch over (recon, dag, epi, red) for fixed storage precisions.
+// block == DSLASH_STAGED: the staged kernel where it applies (plain launches
+// with FP32 links on an uncut lattice whose extents fit its tiles), else the
+// gathering kernel with its default block.
 template <int PG, int PS>
 cudaError_t dispatch_dslash_p(const DslashArgs& A, int recon, bool dag, int epi, bool red, int nrhs, int block,
                               cudaStream_t s)
 {
+    if (block == DSLASH_STAGED) {
+        if constexpr (PG == P32 && PS != P64) {
+            if (!red && epi != EPI_CG && recon == 12 && staged_supported(A.g)) {
+#define LQ_SCASE(DG, EP) \
+    if (dag == DG && epi == EP) return launch_staged_t<PG, PS, 12, DG, EP>(A, nrhs, s);
+                LQ_SCASE(false, EPI_NONE)
+                LQ_SCASE(false, EPI_CLOVINV)
+                LQ_SCASE(false, EPI_XPAY)
+                LQ_SCASE(true, EPI_NONE)
+                LQ_SCASE(true, EPI_CLOVINV)
+                LQ_SCASE(true, EPI_XPAY)
+#undef LQ_SCASE
+            }
+        }
+        block = DSLASH_MAX_BLOCK;
+    }
 #define LQ_CASE(RC, DG, EP, RD)                                                              \
     if (recon == RC && dag == DG && epi == EP && red == RD)                                 \
         return launch_dslash_t<PG, PS, RC, DG, EP, RD>(A, nrhs, block, s);

@@ -99,6 +99,7 @@ _SIGS = {
     "lqcd_harmonic_ritz": [_I, _P, _I, _I, _P, _P],
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
     "lqcd_tune": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "lqcd_tune_set": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
@@ -359,6 +360,18 @@ def lqcd_tune(ctx, prec):
     sites = (C.c_int * 2)()
     _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best, sites), "lqcd_tune")
     return {"block": tuple(best), "sites_per_thread": tuple(sites)}
+
+
+BLOCK_STAGED = 1  # LQCD_BLOCK_STAGED: the shared-memory staged kernel for a plain class
+
+
+def lqcd_tune_set(ctx, prec, block, sites=None):
+    """Set the tuner's choices directly: block = (plain, plain reducing,
+    dagger, dagger reducing), each 32, 64, 96 or 128, or BLOCK_STAGED for the
+    plain ones; sites = (plain reducing, dagger reducing) or None."""
+    b = (C.c_int * 4)(*[int(v) for v in block])
+    s = (C.c_int * 2)(*[int(v) for v in sites]) if sites is not None else None
+    _check(_lib.lqcd_tune_set(ctx, PREC.get(prec, prec), b, s), "lqcd_tune_set")
 
 
 def lqcd_profile_enable(ctx, enable=True):

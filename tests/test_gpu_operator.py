@@ -166,6 +166,66 @@ def test_multi_rhs_matches_single(lq, prec):
             assert torch.equal(single, fout[r * fb:(r + 1) * fb]), ("schur", dag, r)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16spinors", "bf16spinors"])
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (12, 4, 6, 4), (32, 4, 2, 2), (8, 6, 4, 4)])
+def test_staged_kernel_matches_gather_and_oracle(lq, prec, dims):
+    """The shared-memory staged hopping kernel (LQCD_BLOCK_STAGED) gives the
+    gathering kernel's results bit for bit, for the hopping term (both
+    parities, plain and dagger, 3 right-hand sides in one launch) and for the
+    Schur operator whose A^-1 sweeps it runs; and the hop matches the oracle.
+    (8, 6, 4, 4): Ly is no multiple of the tile's 4 rows, so the launch falls
+    back to the gathering kernel.)"""
+    import torch
+    R = 3
+    kappa, csw = 0.13, 1.0
+    U = gauge(dims, "smooth", seed=21)
+    psis = synth.gaussian_spinor(dims, 22, nfields=R)
+    lat = lq.Lattice(dims, max_nrhs=R)
+    lat.gauge_load(U)
+    lat.clover_compute(kappa, csw)
+    fin = lat.new_field(prec, nrhs=R)
+    fg = lat.new_field(prec, nrhs=R)
+    fs = lat.new_field(prec, nrhs=R)
+    gather, staged = (128, 128, 128, 128), (lq.BLOCK_STAGED, 128, lq.BLOCK_STAGED, 128)
+    fb = lat.field_bytes(prec)
+    for par in (0, 1):
+        lat.pack(fin, psis, 1 - par, prec, nrhs=R)
+        for dag in (False, True):
+            fg.fill_(0xff)  # the same bytes in the padding past V/2 sites, which no kernel writes
+            fs.fill_(0xff)
+            lq.lqcd_tune_set(lat.ctx, prec, gather)
+            lat.dslash(fg, fin, par, prec=prec, nrhs=R, dag=dag)
+            lq.lqcd_tune_set(lat.ctx, prec, staged)
+            lat.dslash(fs, fin, par, prec=prec, nrhs=R, dag=dag)
+            torch.cuda.synchronize()
+            assert torch.equal(fg, fs), ("hop", par, dag)
+            out = lat.canonical_spinor()
+            lat.unpack(out, fs[fb:2 * fb], par, prec)
+            torch.cuda.synchronize()
+            assert rel(out.cpu().numpy(), hop_ref(U, psis[1], dims, par, dag=dag)) < TOL[prec], ("oracle", par, dag)
+    lat.pack(fin, psis, 1, prec, nrhs=R)
+    for dag in (False, True):
+        fg.fill_(0xff)
+        fs.fill_(0xff)
+        lq.lqcd_tune_set(lat.ctx, prec, gather)
+        lat.dslash(fg, fin, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec, nrhs=R)
+        lq.lqcd_tune_set(lat.ctx, prec, staged)
+        lat.dslash(fs, fin, 1, kappa, csw, op=lq.OP_SCHUR, dag=dag, prec=prec, nrhs=R)
+        torch.cuda.synchronize()
+        assert torch.equal(fg, fs), ("schur", dag)
+
+
+def test_tune_set_validates(lq):
+    """lqcd_tune_set accepts the tuner's block sizes, and the staged kernel for
+    the plain classes only; it rejects anything else."""
+    lat = lq.Lattice((4, 4, 4, 4))
+    lq.lqcd_tune_set(lat.ctx, "f32", (lq.BLOCK_STAGED, 64, 32, 96), (0, 4))
+    for block, sites in (((lq.BLOCK_STAGED, lq.BLOCK_STAGED, 128, 128), None), ((100, 128, 128, 128), None),
+                         ((128, 128, 128, 128), (-1, 0)), ((128, 128, 128, 128), (0, 65))):
+        with pytest.raises(lq.LqcdError):
+            lq.lqcd_tune_set(lat.ctx, "f32", block, sites)
+
+
 def test_pack_roundtrip(lq):
     dims = (6, 4, 4, 6)
     psi = synth.gaussian_spinor(dims, 15)
@@ -213,7 +273,8 @@ def test_autotuner_keeps_results(lq):
     lat.gauge_load(U)
     for prec in ("f32", "f16"):
         best = lq.lqcd_tune(lat.ctx, prec)
-        assert all(b in (32, 64, 96, 128) for b in best["block"])
+        assert all(b in (32, 64, 96, 128) for b in best["block"][1::2])  # reducing classes
+        assert all(b in (32, 64, 96, 128, lq.BLOCK_STAGED) for b in best["block"][0::2])
         assert all(s in (0, 1, 4, 16) for s in best["sites_per_thread"])
         got = gpu_apply(lat, prec, psi, 1, 0, lambda o, i: lat.dslash(o, i, 0, prec=prec))
         assert rel(got, hop_ref(U, psi, dims, 0)) < TOL[prec]
