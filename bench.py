@@ -245,6 +245,7 @@ def run_ours(args, w, rank, world, local_rank):
         out["e2e"] = e2e_leg(args, lat, b, Vh, params)
         out["solve"] = compare_solves(lat, bd, xd, stream, params)
         out["dslash_f32"] = dslash_microbench(lat, b, dims, stream, hb, hbsrc)
+        out["alu_peaks"] = alu_peaks(local_rank)
     lat.close()
     if rank == 0 and not args.quick:
         del bd, xd
@@ -460,6 +461,16 @@ def dslash_microbench(lat, b, dims, stream, hb, hbsrc):
             "time_roofline_frac": round(comp / t / 1e9 / hb, 4), "peak": hb, "peak_source": hbsrc}
 
 
+def alu_peaks(device):
+    """The device's measured multiply-add peaks (lqcd_fma_peak), TFLOP/s: the
+    denominators of the kernels bound by FP32 or FP64 arithmetic."""
+    from paper_1103_1363_gb300 import lqcd
+    return {"fp32_fma_tflops": round(lqcd.lqcd_fma_peak(device, 0), 1),
+            "fp32x2_fma_tflops": round(lqcd.lqcd_fma_peak(device, 1), 1),
+            "fp64_fma_tflops": round(lqcd.lqcd_fma_peak(device, 2), 3),
+            "source": "measured by lqcd_fma_peak: independent multiply-add chains, 2048 threads per SM"}
+
+
 def run_hop_kernel(args, w):
     """Stand-alone parity hopping term (recon-12) of one precision, for kernel
     profiles: warmup + steps launches over rotating buffer pairs, each holding
@@ -504,8 +515,13 @@ def run_hop_kernel(args, w):
     sb = spinor[args.prec]
     lb = link[args.prec] * (args.recon / 12.0 if args.prec != "f64" else 1)
     comp = (2 * sb * R + 8 * lb) * Vh
+    extra = {}
+    if args.prec == "f64":  # FP64-pipe-bound: the arithmetic roofline as well
+        pk = lqcd.lqcd_fma_peak(torch.cuda.current_device(), 2)
+        extra = {"alu_tflops": round(1320.0 * Vh * R / t / 1e12, 3), "fp64_peak_tflops": round(pk, 3),
+                 "alu_frac": round(1320.0 * Vh * R / t / 1e12 / pk, 4)}
     print(json.dumps({"kernel": "hop", "variant": "staged" if args.staged else "gather", "prec": args.prec,
-                      "recon": args.recon, "nrhs": R,
+                      "recon": args.recon, "nrhs": R, **extra,
                       "workload": workload_name(w),
                       "us_per_launch": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / R, 2),
                       "gflops": round(1320.0 * Vh * R / t / 1e9, 1),
@@ -597,9 +613,11 @@ def run_sap_kernel(args, w):
     stream.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / args.steps
     fl = sap_block_flops(block) * args.nmr * args.ncycle * V
+    pk = lqcd.lqcd_fma_peak(torch.cuda.current_device(), 0)
     out = {"kernel": "sap", "workload": workload_name(w), "block": list(block), "ncycle": args.ncycle,
            "nmr": args.nmr, "ms_per_application": round(t * 1e3, 3),
-           "block_solve_flops_per_application": fl, "block_solve_gflops": round(fl / t / 1e9, 1)}
+           "block_solve_flops_per_application": fl, "block_solve_gflops": round(fl / t / 1e9, 1),
+           "fp32_peak_tflops": round(pk, 1), "alu_frac": round(fl / t / 1e12 / pk, 4)}
     del rs, zs
     if args.quick:
         print(json.dumps(out), flush=True)
@@ -893,7 +911,7 @@ def main():
                                "dslash": r["stats"][-1]["dslash_count"],
                                "true_residual_max": r["worst_res"]},
             "clover_setup_s": r["clover_setup_s"], "tuned": r["tuned"],
-            "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"),
+            "solve": r.get("solve"), "dslash_f32": r.get("dslash_f32"), "alu_peaks": r.get("alu_peaks"),
             "multi_rhs": r.get("multi_rhs"), "learned": r.get("learned"),
         }
         print(json.dumps(line), flush=True)

@@ -458,6 +458,15 @@ lqcd_status lqcd_halo_dslash(lqcd_ctx* ctx, void* out, const void* in, const voi
  * Synchronises the stream. */
 lqcd_status lqcd_norm2(lqcd_ctx* ctx, const void* field, int parity, lqcd_prec prec, int nrhs, double* out);
 
+/* Measured arithmetic peak of GPU `device` in TFLOP/s (2 flops per
+ * multiply-add and lane), the roofline denominator of the kernels bound by
+ * arithmetic rather than by memory: kind 0 = FP32 multiply-add, 1 = FP32
+ * packed two-lane multiply-add, 2 = FP64 multiply-add.  Runs one short and
+ * one ~20 ms launch of independent multiply-add chains on a stream of its own
+ * (allocates and frees a small buffer; synchronises that stream).  The paper
+ * has no counterpart.  LQCD_ERR_INVALID for another kind or a null result. */
+lqcd_status lqcd_fma_peak(int device, int kind, double* tflops);
+
 /* Wait for the context's stream and report device-side errors. */
 lqcd_status lqcd_sync(lqcd_ctx* ctx);
 

@@ -100,6 +100,7 @@ _SIGS = {
     "lqcd_sap_apply": [_P, _P, _P, _P, _I, _I],
     "lqcd_tune": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lqcd_tune_set": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "lqcd_fma_peak": [_I, _I, C.POINTER(C.c_double)],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
@@ -360,6 +361,14 @@ def lqcd_tune(ctx, prec):
     sites = (C.c_int * 2)()
     _check(_lib.lqcd_tune(ctx, PREC.get(prec, prec), best, sites), "lqcd_tune")
     return {"block": tuple(best), "sites_per_thread": tuple(sites)}
+
+
+def lqcd_fma_peak(device, kind):
+    """Measured multiply-add peak of a GPU in TFLOP/s: kind 0 FP32, 1 FP32
+    packed pairs, 2 FP64."""
+    out = C.c_double(0.0)
+    _check(_lib.lqcd_fma_peak(int(device), int(kind), C.byref(out)), "lqcd_fma_peak")
+    return out.value
 
 
 BLOCK_STAGED = 1  # LQCD_BLOCK_STAGED: the shared-memory staged kernel for a plain class

@@ -172,3 +172,16 @@ def test_entry_points_restore_the_current_device(lq):
     assert torch.cuda.current_device() == 0
     lat.clover_compute(0.13, 1.0)
     assert torch.cuda.current_device() == 0
+
+
+def test_fma_peak_measures_and_validates(lq):
+    """lqcd_fma_peak returns positive multiply-add rates (FP64 below FP32, a
+    packed pair at least the scalar rate within noise) and rejects an
+    unknown kind."""
+    f32 = lq.lqcd_fma_peak(0, 0)
+    f32x2 = lq.lqcd_fma_peak(0, 1)
+    f64 = lq.lqcd_fma_peak(0, 2)
+    assert f32 > 1.0 and f64 > 0.0 and f64 < f32
+    assert f32x2 > 0.8 * f32
+    with pytest.raises(lq.LqcdError):
+        lq.lqcd_fma_peak(0, 3)
