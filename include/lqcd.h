@@ -463,7 +463,7 @@ lqcd_status lqcd_norm2(lqcd_ctx* ctx, const void* field, int parity, lqcd_prec p
  * arithmetic rather than by memory: kind 0 = FP32 multiply-add, 1 = FP32
  * packed two-lane multiply-add, 2 = FP64 multiply-add.  Runs one short and
  * one ~20 ms launch of independent multiply-add chains on a stream of its own
- * (allocates and frees a small buffer; synchronises that stream).  The paper
+ * (no device memory is allocated; synchronises that stream).  The paper
  * has no counterpart.  LQCD_ERR_INVALID for another kind or a null result. */
 lqcd_status lqcd_fma_peak(int device, int kind, double* tflops);
 
