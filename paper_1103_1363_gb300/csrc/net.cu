@@ -619,6 +619,185 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// BF16 forward of a layer with one input channel (the network's first layer,
+// and the adjoint of its last): the nine hops' transported inputs, 8 reals
+// each, are laid side by side along K (K = 9 x 8, padded to NC1_K = 80), so
+// that one tile needs one gather, one CTA barrier and 3 x 5 MMAs instead of
+// nine hop stages of 16-wide K of which half is padding.  All four thread
+// groups gather: thread (site sl, group grp) handles hops grp, grp + 4, grp
+// + 8.  The weights of all hops, folded the same way, are built in shared
+// memory once per CTA from the per-hop BF16 weights.  Two X stages: the
+// gather of the next tile runs while the MMAs of this one execute; the
+// accumulator in tensor memory is read out before the next tile's MMAs.
+enum { NC1_KG = 10, NC1_K = 8 * NC1_KG };  // K groups of 8 (9 hops + one zero group)
+
+template <int RECON>
+__global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_c1_kernel(const NetLayerArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N2p = a.N2p;
+    const uint32_t sbo = (uint32_t)NC1_KG * 128;          // bytes between 8-row groups (X and B)
+    const uint32_t blk = (uint32_t)NTC_TS * NC1_K * 2;     // one colour block of X
+    const uint32_t xbytes = 3 * blk;
+    unsigned char* const Bs = smem + 2 * xbytes;           // folded weights [N2p][NC1_K]
+    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(Bs + (size_t)N2p * NC1_K * 2);  // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 2);
+    const uint32_t idesc = tc::idesc_bf16_f32(NTC_TS, N2p);
+    const uint32_t ncols = (uint32_t)a.tmem_cols;
+
+    // zero both X stages (the padding group is never written), fold the weights:
+    // B[n2][8 h + k] = B_h[n2][k] for the 8 real K of each hop (K2p = 16)
+    for (uint32_t e = tid; e < 2 * xbytes / 16; e += NTC_THREADS)
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < NC1_KG * N2p; e += NTC_THREADS) {
+        const int h = e / N2p, n2 = e - h * N2p;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (h < 9) v = *reinterpret_cast<const uint4*>(a.Bh + (size_t)h * N2p * 16 + (n2 / 8) * 128 + (n2 % 8) * 8);
+        *reinterpret_cast<uint4*>(Bs + ((size_t)(n2 / 8) * NC1_KG * 64 + h * 64 + (n2 % 8) * 8) * 2) = v;
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mma_bar[0], 1);
+        tc::mbar_init(&mma_bar[1], 1);
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int ntiles = (a.V + NTC_TS - 1) / NTC_TS;
+    const int total = ntiles * a.batch;
+    const int sl = tid & (NTC_TS - 1), grp = tid / NTC_TS;
+
+    // transported input of the thread's hops for tile t into X stage s
+    auto gather = [&](int t, int s) {
+        const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
+        unsigned char* xrow = smem + s * xbytes + (sl >> 3) * sbo + (sl & 7) * 16;
+        for (int h = grp; h < 9; h += NTC_THREADS / NTC_TS) {
+            float u[18], p[24];
+            float sign = 1.f;
+            int y = -1;
+#pragma unroll
+            for (int k = 0; k < 18; ++k) u[k] = 0.f;  // padding sites: zero link, zero input
+            if (x < a.V) {
+                if (h > 0) {
+                    y = hop_link<RECON>(a, x, h, u, sign);
+#pragma unroll
+                    for (int k = 0; k < 18; ++k) u[k] = sign * u[k];
+                } else {
+                    y = x;
+                }
+            }
+            load_act(a.in, a.in_bf16, a.V, 1, b, 0, y, p);
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) {
+                uint32_t w[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float re, im;
+                    if (h == 0) {
+                        re = p[2 * (3 * r + ca)];
+                        im = p[2 * (3 * r + ca) + 1];
+                    } else {
+                        re = 0.f;
+                        im = 0.f;
+#pragma unroll
+                        for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
+                            const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                            const float pr = p[2 * (3 * r + cb)], pi = p[2 * (3 * r + cb) + 1];
+                            re += ur * pr;
+                            re -= ui * pi;
+                            im += ur * pi;
+                            im += ui * pr;
+                        }
+                    }
+                    w[r] = pack_bf16x2(re, im);
+                }
+                *reinterpret_cast<uint4*>(xrow + ca * blk + h * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    };
+
+    bool failed = false;
+    uint32_t k = 0;  // tiles of this CTA whose MMAs were issued (tile k commits to mma_bar[k & 1])
+    if ((int)blockIdx.x < total) gather(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();  // X stage s complete; the previous tile's accumulator has been read
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t xa = tc::smem_addr(smem + s * xbytes), ba = tc::smem_addr(Bs);
+            for (int ca = 0; ca < 3; ++ca)
+                for (int ks = 0; ks < NC1_K / 16; ++ks)
+                    tc::mma_bf16(tmem + ca * N2p, tc::smem_desc(xa + ca * blk + ks * 256, 128, sbo),
+                                 tc::smem_desc(ba + ks * 256, 128, sbo), idesc, ks > 0 ? 1u : 0u);
+            tc::commit(&mma_bar[s]);
+        }
+        // the next tile's gather overlaps these MMAs (stage 1 - s was last
+        // read by the MMAs of tile k - 1, complete before its epilogue)
+        const int tn = t + gridDim.x;
+        if (tn < total) gather(tn, 1 - s);
+        const bool ok = tc::mbar_wait(&mma_bar[s], (k >> 1) & 1u, NTC_WAIT_NS);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after();
+        // epilogue: as the layer kernel's (warp w reads lanes 32 (w % 4) ..)
+        const int b = t / ntiles, tile0 = (t - b * ntiles) * NTC_TS;
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int site = tile0 + 32 * q4 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+        char* out_item = static_cast<char*>(static_cast<void*>(a.out)) + (size_t)b * act_item_bytes(a.V, a.cout, a.out_bf16);
+        for (int c0 = 16 * wg; c0 < N2p; c0 += 16 * (NTC_THREADS / 128)) {
+            uint32_t v[3][16];
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) tc::ld_x16(trow + ca * N2p + c0, v[ca]);
+            tc::wait_ld();
+            if (site < a.V) {
+#pragma unroll
+                for (int hc = 0; hc < 2; ++hc) {
+                    const int co = c0 / 8 + hc;
+                    if (co >= a.cout) break;
+                    if (a.out_bf16) {
+                        uint4* ob = reinterpret_cast<uint4*>(out_item) + (size_t)co * 3 * a.V + site;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) {
+                                const int kk = 4 * q + m, j = 4 * hc + kk / 3;
+                                w[m] = pack_bf16x2(__uint_as_float(v[kk % 3][2 * j]), __uint_as_float(v[kk % 3][2 * j + 1]));
+                            }
+                            ob[(size_t)q * a.V] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    } else {
+                        float4* out_b = reinterpret_cast<float4*>(out_item);
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            const int k0 = 2 * q, k1 = 2 * q + 1;
+                            const int j0 = 4 * hc + k0 / 3, j1 = 4 * hc + k1 / 3;
+                            out_b[plane4(a.V, co, q) + site] = make_float4(
+                                __uint_as_float(v[k0 % 3][2 * j0]), __uint_as_float(v[k0 % 3][2 * j0 + 1]),
+                                __uint_as_float(v[k1 % 3][2 * j1]), __uint_as_float(v[k1 % 3][2 * j1 + 1]));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (failed) {  // bounded wait for the MMAs of tile k (issued, not seen complete), then free the tensor memory
+        tc::mbar_wait(&mma_bar[k & 1], (k >> 1) & 1u, NTC_WAIT_NS);
+        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
 // BF16 weight gradient of one layer on the tensor cores.  For hop h =
 // blockIdx.y, D[k2][n2] = sum over the (site, colour) rows of X[row][k2]
 // G[row][n2], with X the transported inputs and G the output gradient, both
@@ -1320,7 +1499,16 @@ lqcd_status run_layer(lqcd_net* n, const NetLayerArgs& a0, int batch, int prof_i
         const size_t sm = layer_smem_tc(t);
         int grid = total < sms ? total : sms;
         if (n->max_ctas > 0 && grid > n->max_ctas) grid = n->max_ctas;
-        if (c->cfg.recon == 12) {
+        if (t.cin == 1 && t.nhops == 9 && t.K2p == 16) {  // the hops folded into K
+            const size_t sm1 = (size_t)2 * 3 * NTC_TS * NC1_K * 2 + (size_t)t.N2p * NC1_K * 2 + 2 * 8 + 16;
+            if (c->cfg.recon == 12) {
+                LQ_CUDA(cudaFuncSetAttribute(net_layer_c1_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+                net_layer_c1_kernel<12><<<grid, NTC_THREADS, sm1, c->stream>>>(t);
+            } else {
+                LQ_CUDA(cudaFuncSetAttribute(net_layer_c1_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+                net_layer_c1_kernel<18><<<grid, NTC_THREADS, sm1, c->stream>>>(t);
+            }
+        } else if (c->cfg.recon == 12) {
             LQ_CUDA(cudaFuncSetAttribute(net_layer_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             net_layer_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(t);
         } else {
