@@ -388,7 +388,8 @@ lqcd_status lqcd_sap_apply(lqcd_ctx* ctx, void* z, const void* r, const int bloc
  * CG solver: set-up per lattice, then iteration blocks in lockstep on the
  * stream of ctxs[0] (every context uses it during the call); with
  * params->use_graph one CUDA graph holds the block of every lattice still
- * iterating and is replayed.  Each lattice stops on its own true residual
+ * iterating, each lattice on a parallel branch of its own when the contexts
+ * are distinct (their kernels then run side by side), and is replayed.  Each lattice stops on its own true residual
  * tol[i] (stats[i]).  Returns the first non-OK status of the lattices. */
 lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b,
                              const double* tol, const lqcd_solver_params* params, lqcd_solver_stats* stats);

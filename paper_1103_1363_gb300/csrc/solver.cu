@@ -662,13 +662,46 @@ void destroy_graphs(std::vector<BlockGraph>& cache)
     cache.clear();
 }
 
+// Streams and events that fork the runs of a batch into parallel branches
+// of a captured graph (one branch per run after the first).
+struct Fork {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // [0]: the fork point; [i]: run i's join
+    ~Fork()
+    {
+        for (auto s : streams)
+            if (s) cudaStreamDestroy(s);
+        for (auto e : events)
+            if (e) cudaEventDestroy(e);
+    }
+    lqcd_status init(size_t n)
+    {
+        streams.assign(n, nullptr);
+        events.assign(n, nullptr);
+        for (size_t i = 0; i < n; ++i) {
+            LQ_CUDA(cudaEventCreateWithFlags(&events[i], cudaEventDisableTiming));
+            if (i > 0) LQ_CUDA(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
+        }
+        return LQCD_OK;
+    }
+};
+
 // Iterate every unfinished run in lockstep blocks until all finish or hit
-// maxiter; with graphs, one graph holds the block of every active run.
+// maxiter; with graphs, one graph holds the block of every active run.  The
+// runs of a batch (distinct contexts, hence disjoint memory) are captured as
+// parallel branches, so that the lattices' kernels run side by side: the
+// small lattices of an uneven batch do not fill the GPU one after another.
 lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
 {
     lqcd_ctx* c0 = runs[0]->c;
     const bool persistent = p->persistent != 0;
     const bool graphs = !persistent && p->use_graph && c0->stream != nullptr;
+    bool branches = graphs && runs.size() > 1;
+    for (size_t i = 0; i < runs.size() && branches; ++i)
+        for (size_t j = 0; j < i; ++j)
+            if (runs[i]->c == runs[j]->c) branches = false;
+    Fork fork;
+    if (branches) LQ_TRY(fork.init(runs.size()));
     std::vector<BlockGraph> cache;
     while (true) {
         unsigned long long mask = 0;
@@ -713,17 +746,33 @@ lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
                 cudaGraph_t graph;
                 LQ_CUDA(cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal));
                 lqcd_status cs = LQCD_OK;
-                for (size_t i = 0; i < runs.size() && cs == LQCD_OK; ++i) {
+                cudaError_t fe = cudaSuccess;
+                if (branches) fe = cudaEventRecord(fork.events[0], c0->stream);
+                for (size_t i = 0; i < runs.size() && cs == LQCD_OK && fe == cudaSuccess; ++i) {
                     if (!(mask >> i & 1)) continue;
                     lqcd_ctx* c = runs[i]->c;
+                    const bool branch = branches && i > 0;
+                    if (branch) {  // run i on a branch of its own: fork from c0's stream ...
+                        fe = cudaStreamWaitEvent(fork.streams[i], fork.events[0], 0);
+                        if (fe != cudaSuccess) break;
+                        c->stream = fork.streams[i];
+                    }
                     const long d0 = c->dslash_count, l0 = c->launches;
                     cs = run_block(runs[i]->s, n, ru);
                     e.dslash[i] = c->dslash_count - d0;
                     e.launches[i] = c->launches - l0;
                     c->dslash_count = d0;
                     c->launches = l0;
+                    if (branch) {  // ... and join back into it
+                        if (cs == LQCD_OK) {
+                            fe = cudaEventRecord(fork.events[i], fork.streams[i]);
+                            if (fe == cudaSuccess) fe = cudaStreamWaitEvent(c0->stream, fork.events[i], 0);
+                        }
+                        c->stream = c0->stream;
+                    }
                 }
                 cudaError_t ce = cudaStreamEndCapture(c0->stream, &graph);
+                if (fe != cudaSuccess && ce == cudaSuccess) ce = fe;
                 if (cs != LQCD_OK) { destroy_graphs(cache); return cs; }
                 if (ce != cudaSuccess) { destroy_graphs(cache); return cuda_fail(ce, "cudaStreamEndCapture"); }
                 cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
