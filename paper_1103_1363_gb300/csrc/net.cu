@@ -954,6 +954,161 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_c1_kernel(const NetL
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// BF16 weight gradient of a layer with one output channel (the last layer),
+// all nine hops in one pass.  With X_h(x) = U_h(x) in(x + h) the gradient
+// sum over (x, colour) of conj(X_h) G equals the sum over (y, colour) of
+// conj(in(y)) (T_adj(h) G)(y): the transport moves to the one-channel
+// output gradient (the adjoint hop, which brings G from x = y - h to y), and
+// the input is read once per tile for every hop.  The hops' transported G
+// are folded along N (72 of 80): D[k2][8 h + n'] over the rows (y, colour).
+// One CTA per SM; operands single-buffered; all four thread groups gather.
+template <int RECON>
+__global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_o1_kernel(const NetLayerArgs a, const float* gout, float* gW)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int MX = 128, G4 = NTC_THREADS / NTC_TS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nk = 4 * a.cin;
+    const uint32_t sbox = (MX / 8) * 128, sbog = (uint32_t)NC1_KG * 128;  // bytes between 8-site groups
+    const uint32_t blkx = (uint32_t)NTC_TS * MX * 2, blkg = (uint32_t)NTC_TS * NC1_K * 2;
+    unsigned char* const Xs = smem;
+    unsigned char* const Gs = smem + 3 * blkx;
+    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(Gs + 3 * blkg);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 1);
+    const uint32_t idesc = tc::idesc_bf16_f32(MX, NC1_K) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const uint32_t ncols = (uint32_t)a.tmem_cols;
+
+    for (uint32_t e = tid; e < 3 * (blkx + blkg) / 16; e += NTC_THREADS)  // M and N padding stays zero
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) tc::mbar_init(mma_bar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int ntiles = (a.V + NTC_TS - 1) / NTC_TS;
+    const int total = ntiles * a.batch;
+    const int sl = tid & (NTC_TS - 1), grp = tid / NTC_TS;
+    const uint32_t rowoff = (sl & 7) * 16;
+    uint32_t k = 0;
+    bool wait_failed = false, failed = false;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
+        const int b = t / ntiles, y = (t - b * ntiles) * NTC_TS + sl;
+        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        // A: the input channels grp, grp + 4, ... at the site, untransported
+        for (int ci = grp; ci < a.cin; ci += G4) {
+            float p[24];
+            load_act(a.in, a.in_bf16, a.V, a.cin, b, ci, y < a.V ? y : -1, p);
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) {
+                uint32_t w[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) w[r] = pack_bf16x2(p[2 * (3 * r + ca)], p[2 * (3 * r + ca) + 1]);
+                *reinterpret_cast<uint4*>(Xs + ca * blkx + (sl >> 3) * sbox + ci * 128 + rowoff) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        // B: the output gradient brought to the site by the adjoint of hops grp, grp + 4, grp + 8
+        for (int h = grp; h < 9; h += G4) {
+            float u[18], p[24];
+            float sign = 1.f;
+            int src = -1;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) u[q] = 0.f;  // padding sites: zero link, zero input
+            if (y < a.V) {
+                if (h > 0) {
+                    src = hop_link<RECON>(a, y, adj_hop(h), u, sign);
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) u[q] = sign * u[q];
+                } else {
+                    src = y;
+                }
+            }
+            load_act(gout, a.gout_bf16, a.V, 1, b, 0, src, p);
+#pragma unroll
+            for (int ca = 0; ca < 3; ++ca) {
+                uint32_t w[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float re, im;
+                    if (h == 0) {
+                        re = p[2 * (3 * r + ca)];
+                        im = p[2 * (3 * r + ca) + 1];
+                    } else {
+                        re = 0.f;
+                        im = 0.f;
+#pragma unroll
+                        for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
+                            const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                            const float pr = p[2 * (3 * r + cb)], pi = p[2 * (3 * r + cb) + 1];
+                            re += ur * pr;
+                            re -= ui * pi;
+                            im += ur * pi;
+                            im += ui * pr;
+                        }
+                    }
+                    w[r] = pack_bf16x2(re, im);
+                }
+                *reinterpret_cast<uint4*>(Gs + ca * blkg + (sl >> 3) * sbog + h * 128 + rowoff) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tc::fence_proxy_async();
+        if (__syncthreads_or(wait_failed)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t xa = tc::smem_addr(Xs), ga = tc::smem_addr(Gs);
+            for (int ca = 0; ca < 3; ++ca)
+                for (int ks = 0; ks < NTC_TS / 16; ++ks)
+                    tc::mma_bf16(tmem, tc::smem_desc(xa + ca * blkx + ks * 2 * sbox, sbox, 128),
+                                 tc::smem_desc(ga + ca * blkg + ks * 2 * sbog, sbog, 128), idesc,
+                                 (k > 0 || ca > 0 || ks > 0) ? 1u : 0u);
+            tc::commit(mma_bar);
+        }
+    }
+    if (!failed && k > 0) {
+        const bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (__syncthreads_or(!ok)) failed = true;
+    }
+    if (!failed && k > 0) {
+        tc::fence_after();
+        // lane k2 = 2 kk + {re, im} (input complex kk); column 8 h + 2 n + {re, im}
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int k2 = 32 * q4 + lane;
+        const int kk = k2 >> 1;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+        for (int c0 = 16 * wg; c0 < NC1_K; c0 += 16 * (NTC_THREADS / 128)) {
+            uint32_t v[16];
+            tc::ld_x16(trow + c0, v);
+            tc::wait_ld();
+            float pv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pv[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
+            if ((k2 & 1) == 0 && kk < nk) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int col = c0 + 2 * i, h = col >> 3, n = (col & 7) >> 1;
+                    if (h >= 9) break;
+                    float* dst = gW + (((size_t)h * 4 + n) * nk + kk) * 2;
+                    atomicAdd(dst, __uint_as_float(v[2 * i]) + pv[2 * i + 1]);
+                    atomicAdd(dst + 1, __uint_as_float(v[2 * i + 1]) - pv[2 * i]);
+                }
+            }
+        }
+    }
+    if (failed) {  // bounded wait for this CTA's MMAs in flight, then free the tensor memory
+        if (k > 0) tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
 // BF16 weight gradient of one layer on the tensor cores.  For hop h =
 // blockIdx.y, D[k2][n2] = sum over the (site, colour) rows of X[row][k2]
 // G[row][n2], with X the transported inputs and G the output gradient, both
@@ -1762,7 +1917,20 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
         size_t sm = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 2 * NTC_TS * 19 * 4 + 16;
         if (sm < (size_t)NTC_MIN_SMEM) sm = NTC_MIN_SMEM;
         dim3 grid(per_hop, 9);
-        if (a.cin == 1) {  // all hops in one pass (M = 9 x 8 of 128)
+        if (a.cout == 1 && a.cin <= 16) {  // all hops in one pass, the transport on the output gradient
+            int g1 = total < sms ? total : sms;
+            if (n->max_ctas > 0 && g1 > n->max_ctas) g1 = n->max_ctas;
+            NetLayerArgs o = a;
+            o.tmem_cols = 128;  // NC1_K = 80 columns
+            const size_t sm1 = (size_t)3 * NTC_TS * (128 + NC1_K) * 2 + 8 + 16;
+            if (c->cfg.recon == 12) {
+                LQ_CUDA(cudaFuncSetAttribute(net_wgrad_o1_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+                net_wgrad_o1_kernel<12><<<g1, NTC_THREADS, sm1, c->stream>>>(o, gout, gl);
+            } else {
+                LQ_CUDA(cudaFuncSetAttribute(net_wgrad_o1_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+                net_wgrad_o1_kernel<18><<<g1, NTC_THREADS, sm1, c->stream>>>(o, gout, gl);
+            }
+        } else if (a.cin == 1) {  // all hops in one pass (M = 9 x 8 of 128)
             int g1 = total < sms ? total : sms;
             if (n->max_ctas > 0 && g1 > n->max_ctas) g1 = n->max_ctas;
             const size_t sm1 = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 8 + 16;
