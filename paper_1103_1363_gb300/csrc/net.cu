@@ -1109,6 +1109,224 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_o1_kernel(const NetL
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// BF16 weight gradient of a multi-channel layer, pipelined like the forward:
+// D_h^T[n2][k2] = sum over rows (site, colour) of G[row][n2] X_h[row][k2],
+// so the output gradient G (M = n2, padded to 128) is the A operand and the
+// transported input X_h (N = k2) the B operand.  A CTA takes one group of
+// hops (blockIdx.y: hops 0-4 or 5-8, their accumulators side by side in
+// tensor memory) over a stride of the batch x site tiles of 64 sites.  Each
+// (tile, hop) is a stage: X_h double-buffered, G loaded once per tile (two
+// buffers, by tile parity), the links of the next stage staged by thread
+// group 0 while groups 1-7 gather this stage's channels one item ahead.
+enum { WG_TS = 64, WG_HOPS = 5, WG_MN = 128 };
+
+__device__ __forceinline__ int site_neighbour(const NetLayerArgs& a, int x, int h)
+{
+    const int c0 = x % a.L[0], c1 = (x / a.L[0]) % a.L[1], c2 = (x / (a.L[0] * a.L[1])) % a.L[2],
+              c3 = x / (a.L[0] * a.L[1] * a.L[2]);
+    return hop_neighbour(a, x, c0, c1, c2, c3, h);
+}
+
+template <int RECON>
+__global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_hg_kernel(const NetLayerArgs a, const float* gout, float* gW)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NG = NTC_THREADS / WG_TS;  // 8 thread groups of 64
+    constexpr int TG = NG - 1;               // gathering groups 1..7
+    constexpr int CPT = (NET_MAXC + TG - 1) / TG;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K2p = a.K2p, nk = 4 * a.cin, nn = 4 * a.cout;
+    const int h0 = blockIdx.y * WG_HOPS, nh = (9 - h0) < WG_HOPS ? (9 - h0) : WG_HOPS;
+    const uint32_t sbox = (uint32_t)(K2p / 8) * 128, sbog = (WG_MN / 8) * 128;  // bytes between 8-site groups
+    const uint32_t blkx = (uint32_t)WG_TS * K2p * 2, blkg = (uint32_t)WG_TS * WG_MN * 2;
+    unsigned char* const Xs = smem;                  // [2][3][blkx]
+    unsigned char* const Gs = smem + 6 * blkx;       // [2][3][blkg]
+    float* lbuf = reinterpret_cast<float*>(Gs + 6 * blkg);                        // [2][WG_TS][19]
+    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(lbuf + 2 * WG_TS * 19);       // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 2);
+    const uint32_t idesc = tc::idesc_bf16_f32(WG_MN, K2p) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const uint32_t ncols = (uint32_t)a.tmem_cols;
+
+    for (uint32_t e = tid; e < 6 * (blkx + blkg) / 16; e += NTC_THREADS)  // channel and n2 padding stays zero
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        tc::mbar_init(&mma_bar[0], 1);
+        tc::mbar_init(&mma_bar[1], 1);
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+
+    const int ntiles = (a.V + WG_TS - 1) / WG_TS;
+    const int total = ntiles * a.batch;
+    const int sl = tid & (WG_TS - 1), grp = tid / WG_TS;
+    const uint32_t rowoff = (sl & 7) * 16;
+    const int cfirst = grp - 1;
+    const int nj = (grp > 0 && cfirst < a.cin) ? (a.cin - cfirst + TG - 1) / TG : 0;
+    // links of hop h at site x into slot `slot` (group 0): times the boundary sign, zero past V or for h = 0
+    auto stage_links = [&](int x, int h, int slot) {
+        float un[18];
+        float sign = 1.f;
+        if (x < a.V && h > 0) {
+            hop_link<RECON>(a, x, h, un, sign);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) un[q] = 0.f;
+        }
+        float* ls = lbuf + (slot * WG_TS + sl) * 19;
+#pragma unroll
+        for (int q = 0; q < 18; ++q) ls[q] = sign * un[q];
+    };
+    float nxt[24];
+    if ((int)blockIdx.x < total) {
+        const int t = blockIdx.x, b = t / ntiles, x = (t - b * ntiles) * WG_TS + sl;
+        if (grp == 0) stage_links(x, h0, 0);
+        if (nj > 0) load_act(a.in, a.in_bf16, a.V, a.cin, b, cfirst, x < a.V ? site_neighbour(a, x, h0) : -1, nxt);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    uint32_t g = 0;  // stages whose MMAs were issued (stage g commits to mma_bar[g & 1])
+    int q = 0;       // tiles of this CTA so far
+    bool wait_failed = false, failed = false;
+    for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++q) {
+        const int b = t / ntiles, x = (t - b * ntiles) * WG_TS + sl;
+        const int tn = t + gridDim.x;
+        const int bn = tn / ntiles, xn = (tn - bn * ntiles) * WG_TS + sl;
+        for (int hl = 0; hl < nh; ++hl) {
+            const int h = h0 + hl, s = g & 1;
+            // X stage s (and the G buffer of this tile's parity) is free once stage g - 2's MMAs completed
+            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, NTC_WAIT_NS);
+            // the next stage: hop h + 1 of this tile, else the first hop of the next tile
+            const bool last = hl + 1 == nh;
+            const int xs = last ? xn : x, hs = last ? h0 : h + 1;
+            const bool more = !last || tn < total;
+            if (grp == 0 && more) stage_links(xs, hs, (g + 1) & 1);
+            unsigned char* const Gb = Gs + (q & 1) * 3 * blkg;
+            if (hl == 0) {  // the output gradient at the tile's sites, once per tile
+                for (int co = grp; co < a.cout; co += NG) {
+                    float p[24];
+                    load_act(gout, a.gout_bf16, a.V, a.cout, b, co, x < a.V ? x : -1, p);
+#pragma unroll
+                    for (int ca = 0; ca < 3; ++ca) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) w[r] = pack_bf16x2(p[2 * (3 * r + ca)], p[2 * (3 * r + ca) + 1]);
+                        *reinterpret_cast<uint4*>(Gb + ca * blkg + (sl >> 3) * sbog + co * 128 + rowoff) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+            }
+            float u[18];
+            if (nj > 0) {
+                const float* ls = lbuf + (s * WG_TS + sl) * 19;
+#pragma unroll
+                for (int k = 0; k < 18; ++k) u[k] = ls[k];
+            }
+            const int yh = x < a.V ? site_neighbour(a, x, h) : -1;
+            unsigned char* const Xb = Xs + s * 3 * blkx;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                if (j >= nj) break;
+                const int ci = cfirst + TG * j;
+                float cur[24];
+#pragma unroll
+                for (int k = 0; k < 24; ++k) cur[k] = nxt[k];
+                if (j + 1 < nj) {
+                    load_act(a.in, a.in_bf16, a.V, a.cin, b, ci + TG, yh, nxt);
+                } else if (more) {
+                    load_act(a.in, a.in_bf16, a.V, a.cin, last ? bn : b, cfirst,
+                             xs < a.V ? site_neighbour(a, xs, hs) : -1, nxt);
+                }
+#pragma unroll
+                for (int ca = 0; ca < 3; ++ca) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        float re, im;
+                        if (h == 0) {
+                            re = cur[2 * (3 * r + ca)];
+                            im = cur[2 * (3 * r + ca) + 1];
+                        } else {
+                            re = 0.f;
+                            im = 0.f;
+#pragma unroll
+                            for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
+                                const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
+                                const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
+                                re += ur * pr;
+                                re -= ui * pi;
+                                im += ur * pi;
+                                im += ui * pr;
+                            }
+                        }
+                        w[r] = pack_bf16x2(re, im);
+                    }
+                    *reinterpret_cast<uint4*>(Xb + ca * blkx + (sl >> 3) * sbox + ci * 128 + rowoff) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            tc::fence_proxy_async();
+            if (__syncthreads_or(wait_failed)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t ga = tc::smem_addr(Gb), xa = tc::smem_addr(Xb);
+                for (int ca = 0; ca < 3; ++ca)
+                    for (int ks = 0; ks < WG_TS / 16; ++ks)
+                        tc::mma_bf16(tmem + hl * K2p, tc::smem_desc(ga + ca * blkg + ks * 2 * sbog, sbog, 128),
+                                     tc::smem_desc(xa + ca * blkx + ks * 2 * sbox, sbox, 128), idesc,
+                                     (q > 0 || ca > 0 || ks > 0) ? 1u : 0u);
+                tc::commit(&mma_bar[s]);
+            }
+            ++g;
+        }
+    }
+    if (!failed && g > 0) {
+        const uint32_t gl = g - 1;
+        const bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+        if (__syncthreads_or(!ok)) failed = true;
+    }
+    if (!failed && g > 0) {
+        tc::fence_after();
+        // lane n2 = 2 n + {re, im} (output complex n); column hl K2p + 2 kk + {re, im}
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int n2 = 32 * q4 + lane, n = n2 >> 1;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+        for (int hl = 0; hl < nh; ++hl)
+            for (int c0 = 16 * wg; c0 < K2p; c0 += 16 * (NTC_THREADS / 128)) {
+                uint32_t v[16];
+                tc::ld_x16(trow + hl * K2p + c0, v);
+                tc::wait_ld();
+                float pv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pv[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
+                if ((n2 & 1) == 0 && n < nn) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int kk = (c0 >> 1) + i;
+                        if (kk >= nk) break;
+                        float* dst = gW + (((size_t)(h0 + hl) * nn + n) * nk + kk) * 2;
+                        atomicAdd(dst, __uint_as_float(v[2 * i]) + pv[2 * i + 1]);
+                        atomicAdd(dst + 1, pv[2 * i] - __uint_as_float(v[2 * i + 1]));
+                    }
+                }
+            }
+    }
+    if (failed) {  // bounded wait for this CTA's MMAs in flight, then free the tensor memory
+        if (g > 0) {
+            const uint32_t gl = g - 1;
+            tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+        }
+        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
 // BF16 weight gradient of one layer on the tensor cores.  For hop h =
 // blockIdx.y, D[k2][n2] = sum over the (site, colour) rows of X[row][k2]
 // G[row][n2], with X the transported inputs and G the output gradient, both
@@ -1929,6 +2147,22 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
             } else {
                 LQ_CUDA(cudaFuncSetAttribute(net_wgrad_o1_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
                 net_wgrad_o1_kernel<18><<<g1, NTC_THREADS, sm1, c->stream>>>(o, gout, gl);
+            }
+        } else if (a.cin > 1 && a.K2p * WG_HOPS <= 512) {  // hop groups, pipelined
+            const int per = (sms / 2 > 0 ? sms / 2 : 1);
+            const int tiles = (a.V + WG_TS - 1) / WG_TS * batch;
+            int gx = tiles < per ? tiles : per;
+            if (n->max_ctas > 0 && gx > n->max_ctas) gx = n->max_ctas;
+            NetLayerArgs w = a;
+            w.tmem_cols = 512;
+            const size_t smw = (size_t)6 * WG_TS * (a.K2p + WG_MN) * 2 + (size_t)2 * WG_TS * 19 * 4 + 2 * 8 + 16;
+            dim3 gw(gx, 2);
+            if (c->cfg.recon == 12) {
+                LQ_CUDA(cudaFuncSetAttribute(net_wgrad_hg_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+                net_wgrad_hg_kernel<12><<<gw, NTC_THREADS, smw, c->stream>>>(w, gout, gl);
+            } else {
+                LQ_CUDA(cudaFuncSetAttribute(net_wgrad_hg_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+                net_wgrad_hg_kernel<18><<<gw, NTC_THREADS, smw, c->stream>>>(w, gout, gl);
             }
         } else if (a.cin == 1) {  // all hops in one pass (M = 9 x 8 of 128)
             int g1 = total < sms ? total : sms;
