@@ -803,8 +803,11 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_c1_kernel(const NetL
 // G[row][n2], the hops' transported inputs folded along M (72 of the MMA's
 // 128 rows), so that the output gradient G of a tile is loaded once instead
 // of once per hop.  One CTA per SM over the batch x site tiles, the
-// accumulator in tensor memory across all of them; operands single-buffered
-// as in the per-hop kernel below.  All four thread groups gather.
+// accumulator in tensor memory across all of them; the operands (read by
+// the MMAs as MN-major: M = k2, N = n2, K = the 128 sites of a colour block)
+// are single-buffered.  All four thread groups gather.  The epilogue forms
+// the complex gradient from the real-ified sums:
+//   G_h[n][k] += (D[2k][2n] + D[2k+1][2n+1], D[2k][2n+1] - D[2k+1][2n]).
 template <int RECON>
 __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_c1_kernel(const NetLayerArgs a, const float* gout, float* gW)
 {
@@ -1320,199 +1323,6 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_hg_kernel(const NetL
             const uint32_t gl = g - 1;
             tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
         }
-        if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
-}
-
-// BF16 weight gradient of one layer on the tensor cores.  For hop h =
-// blockIdx.y, D[k2][n2] = sum over the (site, colour) rows of X[row][k2]
-// G[row][n2], with X the transported inputs and G the output gradient, both
-// real-ified BF16 tiles in the forward kernel's layout (rows = sites,
-// 16-byte rows of 8 consecutive k2 or n2 values) and read here as MN-major
-// operands: M = k2 padded to 128, N = n2 padded to 16, K = the 128 sites of
-// a colour block.  All tiles of the CTA accumulate into the same FP32
-// tensor memory.  The epilogue forms the complex gradient
-//   G_h[n][k] += (D[2k][2n] + D[2k+1][2n+1]) + i (D[2k][2n+1] - D[2k+1][2n])
-// (lanes 2k and 2k+1 exchange values by shuffles) and adds it with atomics.
-// Thread (site sl, group grp) loads the input channels grp + 4 j and the
-// output-gradient channels grp + 4 j, one item ahead; group 0 also stages the
-// links of the CTA's next tile.
-template <int RECON>
-__global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_tc_kernel(const NetLayerArgs a, const float* gout, float* gW)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int G4 = NTC_THREADS / NTC_TS, CPT = (NET_MAXC + G4 - 1) / G4;
-    constexpr int MX = 128;  // k2 padded to the MMA's M
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int h = blockIdx.y;
-    const int N2p = a.N2p;
-    const int nk = 4 * a.cin, nn = 4 * a.cout;
-    const uint32_t sbox = (MX / 8) * 128, sbog = (uint32_t)(N2p / 8) * 128;  // bytes between 8-site groups
-    const uint32_t blkx = (uint32_t)NTC_TS * MX * 2, blkg = (uint32_t)NTC_TS * N2p * 2;
-    unsigned char* const Xs = smem;
-    unsigned char* const Gs = smem + 3 * blkx;
-    float* lbuf = reinterpret_cast<float*>(Gs + 3 * blkg);  // [2][NTC_TS][19]
-    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(lbuf + 2 * NTC_TS * 19);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 1);
-    const uint32_t idesc = tc::idesc_bf16_f32(MX, N2p) | (1u << 15) | (1u << 16);  // A and B MN-major
-    const uint32_t ncols = (uint32_t)a.tmem_cols;
-
-    for (uint32_t e = tid; e < 3 * (blkx + blkg) / 16; e += NTC_THREADS)  // K and N padding stays zero
-        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
-    if (tid == 0) tc::mbar_init(mma_bar, 1);
-    if (warp == 0) tc::tmem_alloc(tslot, ncols);
-
-    const int ntiles = (a.V + NTC_TS - 1) / NTC_TS;
-    const int total = ntiles * a.batch;
-    const int sl = tid & (NTC_TS - 1), grp = tid / NTC_TS;
-    const int nX = grp < a.cin ? (a.cin - grp + G4 - 1) / G4 : 0;
-    const int nG = grp < a.cout ? (a.cout - grp + G4 - 1) / G4 : 0;
-    const int nI = nX + nG;
-    // links of hop h (times the boundary sign) for the sites of tile t
-    auto stage_links = [&](int t, int slot) {
-        const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
-        float un[18];
-        float sign = 1.f;
-        if (x < a.V) {
-            hop_link<RECON>(a, x, h, un, sign);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 18; ++q) un[q] = 0.f;
-        }
-        float* ls = lbuf + (slot * NTC_TS + sl) * 19;
-#pragma unroll
-        for (int q = 0; q < 18; ++q) ls[q] = sign * un[q];
-    };
-    // item i of tile t: input channel grp + 4 i at the hop's neighbour, then
-    // output-gradient channel grp + 4 (i - nX) at the site
-    auto load_item = [&](int t, int i, float p[24]) {
-        const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
-        if (i < nX) {
-            int y = -1;
-            if (x < a.V) {
-                const int c0 = x % a.L[0], c1 = (x / a.L[0]) % a.L[1], c2 = (x / (a.L[0] * a.L[1])) % a.L[2],
-                          c3 = x / (a.L[0] * a.L[1] * a.L[2]);
-                y = hop_neighbour(a, x, c0, c1, c2, c3, h);
-            }
-            load_act(a.in, a.in_bf16, a.V, a.cin, b, grp + G4 * i, y, p);
-        } else {
-            load_act(gout, a.gout_bf16, a.V, a.cout, b, grp + G4 * (i - nX), x < a.V ? x : -1, p);
-        }
-    };
-    float nxt[24];
-    if ((int)blockIdx.x < total) {
-        if (grp == 0 && h > 0) stage_links(blockIdx.x, 0);
-        if (nI > 0) load_item(blockIdx.x, 0, nxt);
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tslot;
-
-    int k = 0;  // tiles of this CTA so far (tile k commits once to mma_bar)
-    bool wait_failed = false, failed = false;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
-        const int tn = t + gridDim.x;
-        // the operand tiles are free once the MMAs of tile k - 1 have completed
-        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
-        if (grp == 0 && h > 0 && tn < total) stage_links(tn, (k + 1) & 1);
-        float u[18];
-        if (h > 0 && nX > 0) {
-            const float* ls = lbuf + ((k & 1) * NTC_TS + sl) * 19;
-#pragma unroll
-            for (int q = 0; q < 18; ++q) u[q] = ls[q];
-        }
-        const uint32_t rowoff = (sl & 7) * 16;  // row of the site within its 8-site core matrix
-#pragma unroll
-        for (int i = 0; i < 2 * CPT; ++i) {
-            if (i >= nI) break;
-            float cur[24];
-#pragma unroll
-            for (int q = 0; q < 24; ++q) cur[q] = nxt[q];
-            if (i + 1 < nI) load_item(t, i + 1, nxt);
-            else if (tn < total) load_item(tn, 0, nxt);
-            const bool isx = i < nX;
-            const int ch = grp + G4 * (isx ? i : i - nX);
-            unsigned char* dst = isx ? Xs + (sl >> 3) * sbox + ch * 128 + rowoff
-                                     : Gs + (sl >> 3) * sbog + ch * 128 + rowoff;
-            const uint32_t blk = isx ? blkx : blkg;
-#pragma unroll
-            for (int ca = 0; ca < 3; ++ca) {
-                uint32_t w[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    float re, im;
-                    if (!isx || h == 0) {
-                        re = cur[2 * (3 * r + ca)];
-                        im = cur[2 * (3 * r + ca) + 1];
-                    } else {
-                        re = 0.f;
-                        im = 0.f;
-#pragma unroll
-                        for (int cb = 0; cb < 3; ++cb) {  // one multiply-add per real product
-                            const float ur = u[2 * (3 * ca + cb)], ui = u[2 * (3 * ca + cb) + 1];
-                            const float pr = cur[2 * (3 * r + cb)], pi = cur[2 * (3 * r + cb) + 1];
-                            re += ur * pr;
-                            re -= ui * pi;
-                            im += ur * pi;
-                            im += ui * pr;
-                        }
-                    }
-                    w[r] = pack_bf16x2(re, im);
-                }
-                *reinterpret_cast<uint4*>(dst + ca * blk) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-        tc::fence_proxy_async();
-        if (__syncthreads_or(wait_failed)) {
-            failed = true;
-            break;
-        }
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t xa = tc::smem_addr(Xs), ga = tc::smem_addr(Gs);
-            for (int ca = 0; ca < 3; ++ca)
-                for (int ks = 0; ks < NTC_TS / 16; ++ks)
-                    tc::mma_bf16(tmem, tc::smem_desc(xa + ca * blkx + ks * 2 * sbox, sbox, 128),
-                                 tc::smem_desc(ga + ca * blkg + ks * 2 * sbog, sbog, 128), idesc,
-                                 (k > 0 || ca > 0 || ks > 0) ? 1u : 0u);
-            tc::commit(mma_bar);
-        }
-    }
-    if (!failed && k > 0) {
-        const bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
-        if (__syncthreads_or(!ok)) failed = true;
-    }
-    if (!failed && k > 0) {
-        tc::fence_after();
-        const int q4 = warp & 3, wg = warp >> 2;
-        const int k2 = 32 * q4 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
-        for (int c0 = 16 * wg; c0 < N2p; c0 += 16 * (NTC_THREADS / 128)) {
-            uint32_t v[16];
-            tc::ld_x16(trow + c0, v);
-            tc::wait_ld();
-            float pv[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) pv[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
-            const int kk = k2 >> 1;
-            if ((k2 & 1) == 0 && kk < nk) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int n = c0 / 2 + i;
-                    if (n >= nn) break;
-                    float* dst = gW + (((size_t)h * nn + n) * nk + kk) * 2;
-                    atomicAdd(dst, __uint_as_float(v[2 * i]) + pv[2 * i + 1]);
-                    atomicAdd(dst + 1, __uint_as_float(v[2 * i + 1]) - pv[2 * i]);
-                }
-            }
-        }
-    }
-    if (failed) {  // bounded wait for this CTA's MMAs in flight, then free the tensor memory
-        if (k > 0) tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
         if (tid == 0) atomicOr(a.errw, ERRW_TIMEOUT);
     }
     tc::fence_before();
@@ -2121,7 +1931,9 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
     NetTimed tm;
     LQ_TRY(tm.begin(n, 3 * layer + 2, wb, wf));
     if (n->bf16) {
-        // tensor cores: one CTA per SM, sms / 9 CTAs per hop, each over a stride of the batch x site tiles
+        // tensor cores: one CTA per SM, each over a stride of the batch x site tiles
+        // (one input or one output channel: all nine hops per CTA; otherwise
+        // half the SMs per group of five or four hops)
         const int sms = sm_count();
         if (sms <= 0) return fail(LQCD_ERR_CUDA, "net wgrad: no SM count");
         a.batch = batch;
@@ -2129,13 +1941,7 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
         while (cols < a.N2p) cols *= 2;
         a.tmem_cols = cols;
         const int total = (a.V + NTC_TS - 1) / NTC_TS * batch;
-        int per_hop = sms / 9 > 0 ? sms / 9 : 1;
-        if (per_hop > total) per_hop = total;
-        if (n->max_ctas > 0 && per_hop > n->max_ctas) per_hop = n->max_ctas;
-        size_t sm = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 2 * NTC_TS * 19 * 4 + 16;
-        if (sm < (size_t)NTC_MIN_SMEM) sm = NTC_MIN_SMEM;
-        dim3 grid(per_hop, 9);
-        if (a.cout == 1 && a.cin <= 16) {  // all hops in one pass, the transport on the output gradient
+        if (a.cout == 1) {  // all hops in one pass, the transport on the output gradient
             int g1 = total < sms ? total : sms;
             if (n->max_ctas > 0 && g1 > n->max_ctas) g1 = n->max_ctas;
             NetLayerArgs o = a;
@@ -2148,7 +1954,7 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
                 LQ_CUDA(cudaFuncSetAttribute(net_wgrad_o1_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
                 net_wgrad_o1_kernel<18><<<g1, NTC_THREADS, sm1, c->stream>>>(o, gout, gl);
             }
-        } else if (a.cin > 1 && a.K2p * WG_HOPS <= 512) {  // hop groups, pipelined
+        } else if (a.cin > 1) {  // hop groups, pipelined (K2p <= 96: five hops fit 512 columns)
             const int per = (sms / 2 > 0 ? sms / 2 : 1);
             const int tiles = (a.V + WG_TS - 1) / WG_TS * batch;
             int gx = tiles < per ? tiles : per;
@@ -2164,7 +1970,7 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
                 LQ_CUDA(cudaFuncSetAttribute(net_wgrad_hg_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
                 net_wgrad_hg_kernel<18><<<gw, NTC_THREADS, smw, c->stream>>>(w, gout, gl);
             }
-        } else if (a.cin == 1) {  // all hops in one pass (M = 9 x 8 of 128)
+        } else {  // one input channel: all hops in one pass (M = 9 x 8 of 128)
             int g1 = total < sms ? total : sms;
             if (n->max_ctas > 0 && g1 > n->max_ctas) g1 = n->max_ctas;
             const size_t sm1 = (size_t)3 * NTC_TS * (128 + a.N2p) * 2 + 8 + 16;
@@ -2175,12 +1981,6 @@ lqcd_status run_wgrad(lqcd_net* n, int layer, const float* in, const float* gout
                 LQ_CUDA(cudaFuncSetAttribute(net_wgrad_c1_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
                 net_wgrad_c1_kernel<18><<<g1, NTC_THREADS, sm1, c->stream>>>(a, gout, gl);
             }
-        } else if (c->cfg.recon == 12) {
-            LQ_CUDA(cudaFuncSetAttribute(net_wgrad_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            net_wgrad_tc_kernel<12><<<grid, NTC_THREADS, sm, c->stream>>>(a, gout, gl);
-        } else {
-            LQ_CUDA(cudaFuncSetAttribute(net_wgrad_tc_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            net_wgrad_tc_kernel<18><<<grid, NTC_THREADS, sm, c->stream>>>(a, gout, gl);
         }
         LQ_CUDA(cudaGetLastError());
         c->launches++;
