@@ -652,6 +652,7 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
 lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, const double* const* b,
                              const double* tol, const lqcd_solver_params* params, lqcd_solver_stats* stats)
 {
+    NvtxRange nvtx_range("lqcd_solve_batch");
     LQ_GUARD_BEGIN
     if (!ctxs || !x || !b || !tol || !stats || n < 1) return fail(LQCD_ERR_INVALID, "lqcd_solve_batch: bad argument");
     lqcd_solver_params p;
@@ -675,6 +676,7 @@ lqcd_status lqcd_solve_batch(lqcd_ctx* const* ctxs, int n, double* const* x, con
 
 lqcd_status lqcd_tune(lqcd_ctx* c, lqcd_prec prec, int best_block[4], int best_sites[2])
 {
+    NvtxRange nvtx_range("lqcd_tune");
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     LQ_TRY(check_prec(c, prec));
@@ -807,6 +809,7 @@ lqcd_status lqcd_solver_params_default(lqcd_solver_params* p)
 lqcd_status lqcd_solve(lqcd_ctx* c, double* x, const double* b, double tol, int nrhs, const lqcd_solver_params* params,
                        lqcd_solver_stats* stats)
 {
+    NvtxRange nvtx_range("lqcd_solve");
     LQ_GUARD_BEGIN
     LQ_TRY(check_ready(c));
     if (!x || !b) return fail(LQCD_ERR_INVALID, "lqcd_solve: null vector");

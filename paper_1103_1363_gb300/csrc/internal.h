@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <string>
@@ -32,6 +33,16 @@ lqcd_status cuda_fail(cudaError_t e, const char* where);
 // Makes a device current for the lifetime of the object and gives the
 // calling thread its previous current device back on destruction, so that
 // an entry point never leaves the caller on another GPU.
+// A named NVTX range over a host-side phase (a solve, an iteration block, a
+// network step) for timeline tools; without a tool attached the calls do
+// nothing but test for one.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct DeviceScope {
     int prev = -1;
     lqcd_status enter(int device)

@@ -2317,6 +2317,7 @@ lqcd_status lqcd_net_layer_wgrad(lqcd_net* n, int layer, const float* in, const 
 // out, in: [batch][site][spin][colour] complex (device).
 lqcd_status lqcd_net_forward(lqcd_net* n, float* out, const float* in, int batch)
 {
+    NvtxRange nvtx_range("lqcd_net_forward");
     if (!n || !n->ws || !out || !in) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: bad argument");
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_forward: batch out of range");
     DeviceScope dev_scope;
@@ -2333,6 +2334,7 @@ lqcd_status lqcd_net_forward(lqcd_net* n, float* out, const float* in, int batch
 lqcd_status lqcd_net_train_step(lqcd_net* n, const float* r, const float* e, int batch, double lr, double beta1,
                                 double beta2, double eps, double* loss)
 {
+    NvtxRange nvtx_range("lqcd_net_train_step");
     if (!n || !n->ws || !r || !e) return fail(LQCD_ERR_INVALID, "lqcd_net_train_step: bad argument");
     if (batch < 1 || batch > n->max_batch) return fail(LQCD_ERR_INVALID, "lqcd_net_train_step: batch out of range");
     DeviceScope dev_scope;

@@ -551,6 +551,7 @@ lqcd_status lqcd_set_preconditioner_sap(lqcd_ctx* c, const int block[4], int ncy
 
 lqcd_status lqcd_sap_apply(lqcd_ctx* c, void* z, const void* r, const int block[4], int ncycle, int nmr)
 {
+    NvtxRange nvtx_range("lqcd_sap_apply");
     if (!c || !z || !r || !block) return fail(LQCD_ERR_INVALID, "lqcd_sap_apply: null argument");
     if (!c->ws) return fail(LQCD_ERR_NOMEM, "no workspace: call lqcd_set_workspace");
     if (!c->gauge_loaded) return fail(LQCD_ERR_STATE, "lqcd_sap_apply: no gauge field loaded");

@@ -704,6 +704,7 @@ lqcd_status iterate(std::vector<CgRun*>& runs, const lqcd_solver_params* p)
     if (branches) LQ_TRY(fork.init(runs.size()));
     std::vector<BlockGraph> cache;
     while (true) {
+        NvtxRange nvtx_range("cg iteration block");
         unsigned long long mask = 0;
         int kmax = 0, since = 0, ru_every = 0;
         bool ru_next = false;

@@ -10,12 +10,14 @@ relative error of about 2^-9 (measured 2.3e-3 on every case here); the
 tolerance is 5e-3 for one layer and 6e-3 for a training step's gradient,
 which chains five BF16 contractions (measured 2.5e-3).
 
-The persistent BF16 kernels stride over 128-site tiles (one CTA per SM;
-SMs / 9 CTAs per hop for the weight gradient).  Cases with a CTA cap
-(lqcd_net_set_max_ctas) and the 8^4 x 16 batch make every CTA run several
-tiles, so the next-tile prefetch, the mbarrier phases across tiles and the
-weight gradient's accumulation in tensor memory across tiles are compared
-with the oracle too."""
+The persistent BF16 kernels stride over 128-site tiles (64-site tiles for
+the multi-channel weight gradient; one CTA per SM, or per SM and group of
+hops).  Cases with a CTA cap (lqcd_net_set_max_ctas) and the 8^4 x 16 batch
+make every CTA run several tiles, so the next-tile prefetch, the mbarrier
+phases across tiles and the weight gradients' accumulation in tensor memory
+across tiles are compared with the oracle too.  The one-channel layers (the
+first, and the last one's adjoint and weight gradient) take their own
+folded-hop kernels, which every (1, C, C', 1) case here exercises."""
 import numpy as np
 import pytest
 import torch
@@ -157,3 +159,37 @@ def test_training_reduces_loss(lq):
     losses = [net.train_step(rd, ed, 4, lr=2e-2) for _ in range(150)]
     print("loss %.3e -> %.3e" % (losses[0], losses[-1]))
     assert losses[-1] < 0.05 * losses[0]
+
+
+@pytest.mark.parametrize("bf16", [False, True], ids=["f32", "bf16"])
+def test_network_gauge_equivariance(lq, bf16):
+    """N_{U^g}(g psi) = g N_U(psi) for a random SU(3) gauge transformation g,
+    U^g_mu(x) = g(x) U_mu(x) g(x + mu)^dag: the whole 1-12-12-1 network on
+    the GPU (lqcd_net_forward), FP32 and BF16 tensor-core paths.  The two
+    BF16 runs round different operands, so their bound is a few times the
+    per-layer tolerance; a transport on the wrong side or a missing dagger
+    gives an O(1) difference."""
+    dims = (8, 8, 8, 8)
+    U = synth.smooth_gauge(dims, 0.5, 70)
+    G = synth.random_gauge_transform(dims, 71)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Gf = np.roll(G, -1, axis=3 - mu)
+        Ug[..., mu, :, :] = G @ U[..., mu, :, :] @ np.swapaxes(Gf.conj(), -1, -2)
+    rng = np.random.default_rng(5)
+    chans = (1, 12, 12, 1)
+    w = np.concatenate([rand_w(rng, chans[l + 1], chans[l]).reshape(-1) for l in range(3)])
+    psi = synth.gaussian_spinor(dims, 72)
+    gpsi = np.einsum("...ab,...sb->...sa", G, psi)
+    outs = []
+    for links, src in ((U, psi), (Ug, gpsi)):
+        lat, net = make(lq, chans, bf16, links, max_batch=1, dims=dims)
+        net.set_weights(w)
+        out = torch.empty(psi.shape, dtype=torch.complex64, device="cuda")
+        net.forward(out, dev(src), batch=1)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy().astype(np.complex128))
+    want = np.einsum("...ab,...sb->...sa", G, outs[0])
+    err = rel(outs[1], want)
+    print("equivariance bf16=%d: %.2e" % (bf16, err))
+    assert err < (3 * TOL_BF16_LAYER if bf16 else 1e-5)

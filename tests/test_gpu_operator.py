@@ -278,3 +278,28 @@ def test_autotuner_keeps_results(lq):
         assert all(s in (0, 1, 4, 16) for s in best["sites_per_thread"])
         got = gpu_apply(lat, prec, psi, 1, 0, lambda o, i: lat.dslash(o, i, 0, prec=prec))
         assert rel(got, hop_ref(U, psi, dims, 0)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6), ("f16", 1e-6), ("bf16", 1e-6)])
+def test_norm2_matches_numpy(lq, prec, tol):
+    """lqcd_norm2 (the deterministic two-stage FP64 reduction of the solvers'
+    dots) against numpy's FP64 sum of |psi|^2 over the same stored values:
+    per right-hand side, one parity and both (parity -1); the stored values
+    are read back with lqcd_unpack, so storage rounding cancels out."""
+    import torch
+    dims = (8, 6, 4, 6)
+    R = 3
+    psis = synth.gaussian_spinor(dims, 23, nfields=R)
+    lat = lq.Lattice(dims, max_nrhs=R)
+    for par in (0, 1, -1):
+        f = lat.new_field(prec, nrhs=R, full=(par == -1))
+        lat.pack(f, psis, par, prec, nrhs=R)
+        got = lq.lqcd_norm2(lat.ctx, f, par, prec, nrhs=R)
+        fb = lat.field_bytes(prec) * (2 if par == -1 else 1)
+        for r in range(R):
+            out = lat.canonical_spinor()
+            out.zero_()
+            lat.unpack(out, f[r * fb:(r + 1) * fb], par, prec)
+            torch.cuda.synchronize()
+            want = float(np.sum(np.abs(out.cpu().numpy()) ** 2))
+            assert abs(got[r] - want) <= tol * want, (prec, par, r, got[r], want)
