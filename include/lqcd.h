@@ -46,8 +46,8 @@
  * human-readable message for the last failure on the calling thread is
  * available from lqcd_last_error().  Calls are asynchronous on the
  * context's stream; device-side problems (a singular clover block, a solver
- * breakdown) are recorded in a device error word and reported by lqcd_sync
- * or at the end of a solve.  A context is not thread-safe; separate
+ * breakdown, an expired bounded wait) are recorded in a device error word
+ * and reported, then cleared, by lqcd_sync, or at the end of a solve.  A context is not thread-safe; separate
  * contexts may be used concurrently.
  */
 #ifndef LQCD_H
@@ -313,13 +313,23 @@ lqcd_status lqcd_net_set_workspace(lqcd_net* net, void* dev_ptr, size_t bytes);
 lqcd_status lqcd_net_bind(lqcd_net* net, lqcd_ctx* ctx);
 /* Cap the CTAs of the BF16 network's persistent launches: at most max_ctas
  * CTAs for a layer (forward or adjoint; by default one per SM, each striding
- * over the batch x 128-site tiles) and at most max_ctas CTAs per hop for the
- * weight gradient (default SMs / 9); the FP32 weight gradient takes the same
- * cap per hop.  0 restores the defaults.  Results do not depend on the cap
+ * over the batch x 128-site tiles) and for a weight gradient (one input or
+ * output channel: all hops per CTA, default one CTA per SM; otherwise at
+ * most max_ctas per group of hops, default SMs / 2); the FP32 weight
+ * gradient takes the same cap per hop.  0 restores the defaults.  Results do not depend on the cap
  * beyond the FP32 summation order of the weight gradient's atomics; a small
  * cap makes every CTA run many tiles (tests use it to check the multi-tile
  * path on small lattices).  LQCD_ERR_INVALID for max_ctas < 0. */
 lqcd_status lqcd_net_set_max_ctas(lqcd_net* net, int max_ctas);
+/* Bound of the BF16 network kernels' waits on their own tensor-core MMAs and
+ * copies (mbarriers): limit_ns > 0 sets it, 0 restores the default of 2 s.
+ * A wait that runs out sets the device error word (lqcd_sync then returns
+ * LQCD_ERR_TIMEOUT); the CTA waits, with the default bound, for its own
+ * operations in flight, frees its tensor memory and exits, and the network
+ * stays usable.  expire_test = 1 is a test of that path: each CTA's last
+ * wait of a launch is then for an mbarrier phase that nothing completes, so
+ * it runs out after limit_ns.  LQCD_ERR_INVALID for a null network. */
+lqcd_status lqcd_net_set_wait(lqcd_net* net, unsigned long long limit_ns, int expire_test);
 /* Complex weights in all: the sum over layers of 9 x 4 C_out x 4 C_in. */
 lqcd_status lqcd_net_num_weights(const lqcd_net* net, size_t* complex_count);
 /* w: host or device FP32 complex weights (resets the Adam moments). */

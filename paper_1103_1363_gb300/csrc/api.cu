@@ -642,6 +642,7 @@ lqcd_status lqcd_sync(lqcd_ctx* c)
     int err = 0;
     LQ_CUDA(cudaMemcpyAsync(&err, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LQ_CUDA(cudaStreamSynchronize(c->stream));
+    if (err) LQ_CUDA(cudaMemsetAsync(c->errw, 0, sizeof(int), c->stream));  // reported once
     if (err & ERRW_CLOVER_SINGULAR) return fail(LQCD_ERR_CLOVER_SINGULAR, "singular clover block");
     if (err & ERRW_BREAKDOWN) return fail(LQCD_ERR_BREAKDOWN, "solver breakdown");
     if (err & ERRW_TIMEOUT) return fail(LQCD_ERR_TIMEOUT, "a bounded device wait expired");

@@ -61,6 +61,8 @@ struct NetLayerArgs {
     int out_bf16;
     int gout_bf16;     // weight gradient: the output gradient in BF16 planes
     int nhops;         // tensor-core layer: hops 0 .. nhops - 1 (9; 1 for the stacked contraction)
+    unsigned long long wait_ns;  // bound of the tensor-core kernels' mbarrier waits
+    int expire_test;   // test of the expiry path: each CTA's last wait is for a phase that never completes
 };
 
 __host__ __device__ inline int adj_hop(int h) { return h == 0 ? 0 : (h % 2 == 1 ? h + 1 : h - 1); }
@@ -380,8 +382,10 @@ __device__ __forceinline__ void load_act(const void* act, int bf, int V, int ch,
     else load_channel(reinterpret_cast<const float*>(item), V, ci, y, p);
 }
 
-// Upper bound of any wait on this kernel's own MMAs (a hop's MMAs take
-// microseconds); an expired wait sets ERRW_TIMEOUT and the CTA stops.
+// Default bound of a wait on the kernels' own MMAs and copies (a hop's MMAs
+// take microseconds); an expired wait sets ERRW_TIMEOUT and the CTA stops,
+// after waiting (with this bound) for its own operations in flight and
+// freeing its tensor memory.
 #define NTC_WAIT_NS 2000000000ull
 
 // BF16 forward of one layer on the tensor cores.  Shared memory: two
@@ -456,7 +460,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
             unsigned char* const Bst = smem + 2 * xbytes + s * bbytes;  // stage s: B_h
             // stage s is free once the MMAs of hop g - 2 have completed (each
             // thread waits for itself; a failure is shared at the barrier below)
-            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, NTC_WAIT_NS);
+            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, a.wait_ns);
             if (grp == 0 && h + 1 < a.nhops) {  // links of hop h + 1 (read after this hop's barrier)
                 float un[18];
                 float sign = 1.f;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
                 }
             }
             tc::fence_proxy_async();
-            if (!wait_failed) wait_failed = !tc::mbar_wait(&b_bar[s], (g >> 1) & 1u, NTC_WAIT_NS);
+            if (!wait_failed) wait_failed = !tc::mbar_wait(&b_bar[s], (g >> 1) & 1u, a.wait_ns);
             if (__syncthreads_or(wait_failed)) {
                 failed = true;
                 break;
@@ -547,7 +551,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_tc_kernel(const NetL
         if (failed) break;
         {  // the tile's last MMAs (their commit covers every earlier one)
             const uint32_t gl = g - 1;
-            const bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+            bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, a.wait_ns);
+            // expiry test: then wait for the next phase, which nothing completes
+            if (ok && a.expire_test) ok = tc::mbar_wait(&mma_bar[gl & 1], ((gl >> 1) & 1u) ^ 1u, a.wait_ns);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -740,7 +746,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_layer_c1_kernel(const NetL
         // read by the MMAs of tile k - 1, complete before its epilogue)
         const int tn = t + gridDim.x;
         if (tn < total) gather(tn, 1 - s);
-        const bool ok = tc::mbar_wait(&mma_bar[s], (k >> 1) & 1u, NTC_WAIT_NS);
+        bool ok = tc::mbar_wait(&mma_bar[s], (k >> 1) & 1u, a.wait_ns);
+        // expiry test: then wait for the next phase, which nothing completes
+        if (ok && a.expire_test) ok = tc::mbar_wait(&mma_bar[s], ((k >> 1) & 1u) ^ 1u, a.wait_ns);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -843,7 +851,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_c1_kernel(const NetL
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
         const int b = t / ntiles, x = (t - b * ntiles) * NTC_TS + sl;
         // the operand tiles are free once the MMAs of tile k - 1 have completed
-        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, a.wait_ns);
         // X: the transported input of hops grp, grp + 4, grp + 8 at M rows 8 h .. 8 h + 7
         for (int h = grp; h < 9; h += G4) {
             float u[18], p[24];
@@ -919,7 +927,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_c1_kernel(const NetL
         }
     }
     if (!failed && k > 0) {
-        const bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, a.wait_ns);
+        // expiry test: then wait for the next phase, which nothing completes
+        if (ok && a.expire_test) ok = tc::mbar_wait(mma_bar, ((k - 1) & 1) ^ 1u, a.wait_ns);
         if (__syncthreads_or(!ok)) failed = true;
     }
     if (!failed && k > 0) {
@@ -998,7 +1008,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_o1_kernel(const NetL
     bool wait_failed = false, failed = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++k) {
         const int b = t / ntiles, y = (t - b * ntiles) * NTC_TS + sl;
-        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        if (k >= 1 && !wait_failed) wait_failed = !tc::mbar_wait(mma_bar, (k - 1) & 1, a.wait_ns);
         // A: the input channels grp, grp + 4, ... at the site, untransported
         for (int ci = grp; ci < a.cin; ci += G4) {
             float p[24];
@@ -1074,7 +1084,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_o1_kernel(const NetL
         }
     }
     if (!failed && k > 0) {
-        const bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, NTC_WAIT_NS);
+        bool ok = tc::mbar_wait(mma_bar, (k - 1) & 1, a.wait_ns);
+        // expiry test: then wait for the next phase, which nothing completes
+        if (ok && a.expire_test) ok = tc::mbar_wait(mma_bar, ((k - 1) & 1) ^ 1u, a.wait_ns);
         if (__syncthreads_or(!ok)) failed = true;
     }
     if (!failed && k > 0) {
@@ -1199,7 +1211,7 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_hg_kernel(const NetL
         for (int hl = 0; hl < nh; ++hl) {
             const int h = h0 + hl, s = g & 1;
             // X stage s (and the G buffer of this tile's parity) is free once stage g - 2's MMAs completed
-            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, NTC_WAIT_NS);
+            if (g >= 2 && !wait_failed) wait_failed = !tc::mbar_wait(&mma_bar[s], ((g - 2) >> 1) & 1u, a.wait_ns);
             // the next stage: hop h + 1 of this tile, else the first hop of the next tile
             const bool last = hl + 1 == nh;
             const int xs = last ? xn : x, hs = last ? h0 : h + 1;
@@ -1289,7 +1301,9 @@ __global__ void __launch_bounds__(NTC_THREADS, 1) net_wgrad_hg_kernel(const NetL
     }
     if (!failed && g > 0) {
         const uint32_t gl = g - 1;
-        const bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, NTC_WAIT_NS);
+        bool ok = tc::mbar_wait(&mma_bar[gl & 1], (gl >> 1) & 1u, a.wait_ns);
+        // expiry test: then wait for the next phase, which nothing completes
+        if (ok && a.expire_test) ok = tc::mbar_wait(&mma_bar[gl & 1], ((gl >> 1) & 1u) ^ 1u, a.wait_ns);
         if (__syncthreads_or(!ok)) failed = true;
     }
     if (!failed && g > 0) {
@@ -1719,6 +1733,8 @@ struct lqcd_net {
     size_t boff[8], bhoff[8];
     long adam_t;
     int max_ctas;          // cap on the CTAs of the persistent tensor-core launches (0: one per SM)
+    unsigned long long wait_ns = NTC_WAIT_NS;  // bound of the tensor-core kernels' mbarrier waits
+    int expire_test = 0;   // lqcd_net_set_wait's test of the expiry path
     size_t nW() const { return woff[nlayers]; }
 };
 
@@ -1752,6 +1768,8 @@ NetLayerArgs layer_args(const lqcd_net* n, int l, bool adjoint, const float* in,
     while (cols < 3 * a.N2p) cols *= 2;
     a.tmem_cols = cols;
     a.errw = c->errw;
+    a.wait_ns = n->wait_ns;
+    a.expire_test = n->expire_test;
     a.in_bf16 = n->bf16 && a.cin > 1;   // multi-channel activations of the BF16 network: BF16 planes
     a.out_bf16 = n->bf16 && a.cout > 1;
     a.nhops = 9;
@@ -2250,6 +2268,14 @@ lqcd_status lqcd_net_set_max_ctas(lqcd_net* n, int max_ctas)
     if (!n) return fail(LQCD_ERR_INVALID, "lqcd_net_set_max_ctas: null network");
     if (max_ctas < 0) return fail(LQCD_ERR_INVALID, "lqcd_net_set_max_ctas: max_ctas must be >= 0");
     n->max_ctas = max_ctas;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_net_set_wait(lqcd_net* n, unsigned long long limit_ns, int expire_test)
+{
+    if (!n) return fail(LQCD_ERR_INVALID, "lqcd_net_set_wait: null network");
+    n->wait_ns = limit_ns > 0 ? limit_ns : NTC_WAIT_NS;
+    n->expire_test = expire_test ? 1 : 0;
     return LQCD_OK;
 }
 

@@ -101,6 +101,7 @@ _SIGS = {
     "lqcd_tune": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lqcd_tune_set": [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lqcd_fma_peak": [_I, _I, C.POINTER(C.c_double)],
+    "lqcd_net_set_wait": [_P, C.c_ulonglong, _I],
     "lqcd_solve_batch": [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D),
                          C.POINTER(lqcd_solver_params), C.POINTER(lqcd_solver_stats)],
     "lqcd_net_create": [_P, _I, _P, _I, _I, C.POINTER(_P)],
@@ -476,6 +477,11 @@ class Net:
         _check(_lib.lqcd_net_get_weights(self.h, _ptr(w), _ptr(g) if grad else None),
                "lqcd_net_get_weights")
         return (w, g) if grad else w
+
+    def set_wait(self, limit_ns=0, expire_test=False):
+        """Bound of the tensor-core kernels' waits (0: the default 2 s);
+        expire_test makes each CTA's last wait run out (test of that path)."""
+        _check(_lib.lqcd_net_set_wait(self.h, int(limit_ns), int(bool(expire_test))), "lqcd_net_set_wait")
 
     def layer_apply(self, layer, out, inp, batch=1, adjoint=False):
         _check(_lib.lqcd_net_layer_apply(self.h, int(layer), int(bool(adjoint)), _ptr(out), _ptr(inp),

@@ -193,3 +193,45 @@ def test_network_gauge_equivariance(lq, bf16):
     err = rel(outs[1], want)
     print("equivariance bf16=%d: %.2e" % (bf16, err))
     assert err < (3 * TOL_BF16_LAYER if bf16 else 1e-5)
+
+
+def test_expired_wait_is_reported_and_net_stays_usable(lq):
+    """The tensor-core kernels' bounded mbarrier waits: with
+    lqcd_net_set_wait's expiry test each CTA's last wait is for a phase that
+    nothing completes, bounded by 1 ms, so it runs out; the CTA then waits for
+    its own MMAs and copies, frees its tensor memory and exits.  lqcd_sync
+    reports LQCD_ERR_TIMEOUT (once), after a forward (the folded first layer,
+    the 12 -> 12 layer, the stacked 12 -> 1 contraction) and after a training
+    step (the three weight-gradient kernels); with the default bound and the
+    weights set again the same network then reproduces its earlier output bit
+    for bit."""
+    dims = (8, 8, 8, 8)
+    U = synth.smooth_gauge(dims, 0.5, 80)
+    rng = np.random.default_rng(6)
+    chans = (1, 12, 12, 1)
+    lat, net = make(lq, chans, True, U, max_batch=2, dims=dims)
+    w = np.concatenate([rand_w(rng, chans[l + 1], chans[l]).reshape(-1) for l in range(3)])
+    net.set_weights(w)
+    psi = dev(synth.gaussian_spinor(dims, 81))
+    ref = torch.empty_like(psi)
+    net.forward(ref, psi, batch=1)
+    lat.sync()
+    net.set_wait(1_000_000, expire_test=True)
+    out = torch.empty_like(psi)
+    net.forward(out, psi, batch=1)
+    with pytest.raises(lq.LqcdError) as e:
+        lat.sync()
+    assert e.value.status == 7
+    lat.sync()  # reported once
+    r = dev(field(dims, 1, 82, 2)[:, :, :, :, :, 0])
+    t = dev(field(dims, 1, 83, 2)[:, :, :, :, :, 0])
+    net.train_step(r, t, 2, lr=0.0)
+    with pytest.raises(lq.LqcdError) as e:
+        lat.sync()
+    assert e.value.status == 7
+    net.set_wait(0, expire_test=False)
+    net.set_weights(w)  # the aborted step's Adam moments and weights are not to be trusted
+    out = torch.empty_like(psi)
+    net.forward(out, psi, batch=1)
+    lat.sync()
+    assert torch.equal(out, ref)
