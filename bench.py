@@ -242,18 +242,29 @@ def run_ours(args, w, rank, world, local_rank):
            "clover_setup_s": round(clover_s, 3), "prof": prof, "tuned": tuned}
 
     if rank == 0 and not args.quick:
-        out["e2e"] = e2e_leg(args, lat, b, Vh, params)
-        out["solve"] = compare_solves(lat, bd, xd, stream, params)
-        out["dslash_f32"] = dslash_microbench(lat, b, dims, stream, hb, hbsrc)
-        out["alu_peaks"] = alu_peaks(local_rank)
+        out["e2e"] = guarded("e2e", e2e_leg, args, lat, b, Vh, params)
+        out["solve"] = guarded("solve", compare_solves, lat, bd, xd, stream, params)
+        out["dslash_f32"] = guarded("dslash_f32", dslash_microbench, lat, b, dims, stream, hb, hbsrc)
+        out["alu_peaks"] = guarded("alu_peaks", alu_peaks, local_rank)
     lat.close()
     if rank == 0 and not args.quick:
         del bd, xd
         torch.cuda.empty_cache()
-        out["multi_rhs"] = multi_rhs_leg(dev)
+        out["multi_rhs"] = guarded("multi_rhs", multi_rhs_leg, dev)
         if not args.skip_learned:
-            out["learned"] = learned_leg(dev)
+            out["learned"] = guarded("learned", learned_leg, dev)
     return out
+
+
+def guarded(name, fn, *args):
+    """A comparison leg: its failure is reported in its place (and on
+    stderr) instead of costing the run its JSON line."""
+    try:
+        return fn(*args)
+    except Exception as ex:  # noqa: BLE001 - any failure of a side measurement
+        msg = "%s: %s" % (type(ex).__name__, ex)
+        print("bench: leg %s failed: %s" % (name, msg), file=sys.stderr, flush=True)
+        return {"error": msg[:300]}
 
 
 def e2e_leg(args, lat, b, Vh, params):
