@@ -39,28 +39,51 @@ namespace lqcd {
 
 lqcd_status net_apply_internal(lqcd_net* n, void* z, const void* r, size_t rb);
 
-enum { GCR_KMAX = 24, GCR_NDOT = 2 * GCR_KMAX + 3 };
+enum { GCR_KMAX = 24, GCR_NDOT = 2 * GCR_KMAX + 8 };  // the last chunk writes 8 values at 2 GCR_KMAX
 constexpr double GCR_CYCLE_REDUCTION = 1e-5;
 
-// out[2j, 2j+1] = <w_j, w_k> (j < k), out[2k, 2k+1] = <w_k, r>,
-// out[2k+2] = |w_k|^2.  FP32 sums per thread, FP64 across threads.
+// out[2j, 2j+1] = <w_j, w_k> (j < k), out[2 KMAX, 2 KMAX + 1] = <w_k, r>,
+// out[2 KMAX + 2] = |w_k|^2.  The dots are split over blockIdx.y in chunks
+// of GCR_CH basis vectors (chunk c < nch_j: j = c GCR_CH ..; the last chunk
+// the dots with r), each with its own partials, ticket and eight outputs, so
+// that a thread loads at most GCR_CH + 1 fields per site instead of k + 2 in
+// a chain.  FP32 sums per thread, FP64 across threads.
+enum { GCR_CH = 4 };
+
 __global__ void gcr_dots_kernel(Geom g, const char* W, size_t fld, int k, const char* wk, const char* r,
-                                double* partials, unsigned* ticket, double* out)
+                                double* partials, unsigned* tickets, double* out)
 {
-    float acc[GCR_NDOT];
+    const int c = blockIdx.y, nch_j = (k + GCR_CH - 1) / GCR_CH;
+    const bool with_r = c == nch_j;
+    const int j0 = c * GCR_CH, cnt = with_r ? 0 : min(GCR_CH, k - j0);
+    float acc[2 * GCR_CH];
 #pragma unroll
-    for (int j = 0; j < GCR_NDOT; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 2 * GCR_CH; ++j) acc[j] = 0.f;
     const size_t fb = fld / 2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
         for (int par = 0; par < 2; ++par) {
-            float vv[24], rv[24];
+            float vv[24];
             SpinorIO<P32>::load(wk + par * fb, g.stride, i, vv);
-            SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
+            if (with_r) {
+                float rv[24];
+                SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
+                float re = 0.f, im = 0.f, nn = 0.f;
 #pragma unroll
-            for (int j = 0; j < GCR_KMAX; ++j) {
-                if (j >= k) break;
+                for (int q = 0; q < 12; ++q) {
+                    re += vv[2 * q] * rv[2 * q] + vv[2 * q + 1] * rv[2 * q + 1];
+                    im += vv[2 * q] * rv[2 * q + 1] - vv[2 * q + 1] * rv[2 * q];
+                    nn += vv[2 * q] * vv[2 * q] + vv[2 * q + 1] * vv[2 * q + 1];
+                }
+                acc[0] += re;
+                acc[1] += im;
+                acc[2] += nn;
+                continue;
+            }
+#pragma unroll
+            for (int j = 0; j < GCR_CH; ++j) {
+                if (j >= cnt) break;
                 float w[24];
-                SpinorIO<P32>::load(W + j * fld + par * fb, g.stride, i, w);
+                SpinorIO<P32>::load(W + (size_t)(j0 + j) * fld + par * fb, g.stride, i, w);
                 float re = 0.f, im = 0.f;
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
@@ -70,21 +93,12 @@ __global__ void gcr_dots_kernel(Geom g, const char* W, size_t fld, int k, const 
                 acc[2 * j] += re;
                 acc[2 * j + 1] += im;
             }
-            float re = 0.f, im = 0.f, nn = 0.f;
-#pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                re += vv[2 * q] * rv[2 * q] + vv[2 * q + 1] * rv[2 * q + 1];
-                im += vv[2 * q] * rv[2 * q + 1] - vv[2 * q + 1] * rv[2 * q];
-                nn += vv[2 * q] * vv[2 * q] + vv[2 * q + 1] * vv[2 * q + 1];
-            }
-            acc[2 * GCR_KMAX] += re;
-            acc[2 * GCR_KMAX + 1] += im;
-            acc[2 * GCR_KMAX + 2] += nn;
         }
-    double d[GCR_NDOT];
+    double d[2 * GCR_CH];
 #pragma unroll
-    for (int j = 0; j < GCR_NDOT; ++j) d[j] = acc[j];
-    block_reduce_finalize<GCR_NDOT>(d, partials, ticket, out);
+    for (int j = 0; j < 2 * GCR_CH; ++j) d[j] = acc[j];
+    block_reduce_finalize<2 * GCR_CH>(d, partials + (size_t)c * gridDim.x * 2 * GCR_CH, tickets + c,
+                                      out + (with_r ? 2 * GCR_KMAX : 2 * j0));
 }
 
 struct GcrStep {
@@ -97,41 +111,40 @@ struct GcrStep {
 __global__ void gcr_orth_update_kernel(Geom g, const char* W, size_t fld, int k, char* wk, char* r, GcrStep st,
                                        double* partials, unsigned* ticket, double* out)
 {
+    // one thread per (parity, float4 chunk, site): the update is elementwise,
+    // so six threads share a site, each running the chain of k loads for its
+    // chunk (six times the loads in flight of a thread per site)
     double acc[2] = {0.0, 0.0};
     const size_t fb = fld / 2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.Vh; i += gridDim.x * blockDim.x)
-        for (int par = 0; par < 2; ++par) {
-            float a[24];
-            SpinorIO<P32>::load(wk + par * fb, g.stride, i, a);
-            for (int j = 0; j < k; ++j) {
-                float w[24];
-                SpinorIO<P32>::load(W + j * fld + par * fb, g.stride, i, w);
-                const float xr = st.c[j].x, xi = st.c[j].y;
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    a[2 * q] -= xr * w[2 * q] - xi * w[2 * q + 1];
-                    a[2 * q + 1] -= xr * w[2 * q + 1] + xi * w[2 * q];
-                }
-            }
-            if (k > 0) SpinorIO<P32>::store(wk + par * fb, g.stride, i, a);
-            float nw = 0.f, nr = 0.f;
-#pragma unroll
-            for (int q = 0; q < 24; ++q) nw += a[q] * a[q];
-            if (st.update_r) {
-                float rv[24];
-                SpinorIO<P32>::load(r + par * fb, g.stride, i, rv);
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    rv[2 * q] -= st.a.x * a[2 * q] - st.a.y * a[2 * q + 1];
-                    rv[2 * q + 1] -= st.a.x * a[2 * q + 1] + st.a.y * a[2 * q];
-                }
-                SpinorIO<P32>::store(r + par * fb, g.stride, i, rv);
-#pragma unroll
-                for (int q = 0; q < 24; ++q) nr += rv[q] * rv[q];
-            }
-            acc[0] += nr;
-            acc[1] += nw;
+    const long n = 12L * g.Vh;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int pq = (int)(e / g.Vh), i = (int)(e - (long)pq * g.Vh);
+        const int par = pq / 6, q = pq - 6 * par;
+        const size_t off = par * fb + ((size_t)q * g.stride + i) * sizeof(float4);
+        float4 a = *reinterpret_cast<const float4*>(wk + off);
+        for (int j = 0; j < k; ++j) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(W + j * fld + off));
+            const float xr = st.c[j].x, xi = st.c[j].y;
+            a.x -= xr * w.x - xi * w.y;
+            a.y -= xr * w.y + xi * w.x;
+            a.z -= xr * w.z - xi * w.w;
+            a.w -= xr * w.w + xi * w.z;
         }
+        if (k > 0) *reinterpret_cast<float4*>(wk + off) = a;
+        const float nw = a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+        float nr = 0.f;
+        if (st.update_r) {
+            float4 rv = *reinterpret_cast<const float4*>(r + off);
+            rv.x -= st.a.x * a.x - st.a.y * a.y;
+            rv.y -= st.a.x * a.y + st.a.y * a.x;
+            rv.z -= st.a.x * a.z - st.a.y * a.w;
+            rv.w -= st.a.x * a.w + st.a.y * a.z;
+            *reinterpret_cast<float4*>(r + off) = rv;
+            nr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+        }
+        acc[0] += nr;
+        acc[1] += nw;
+    }
     block_reduce_finalize<2>(acc, partials, ticket, out);
 }
 
@@ -196,7 +209,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     double* dev = reinterpret_cast<double*>(X32 + fld);  // scalars of the recursion
     double* dots = dev;                                    // [GCR_NDOT]
     double* upd = dev + 64;                                // [2]
-    unsigned* tick = reinterpret_cast<unsigned*>(upd + 4); // [1]
+    unsigned* tick = reinterpret_cast<unsigned*>(upd + 4); // [0]: updates, [1 + c]: dot chunk c
     double* parts = reinterpret_cast<double*>(reinterpret_cast<char*>(tick) + 256);
     const size_t canon_rb = (size_t)c->volume * 192;
 
@@ -209,7 +222,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     }
     LQ_TRY(pack_spinor(c, B, bdev, -1, P64, 1, rb64, canon_rb));
     LQ_CUDA(cudaMemsetAsync(c->scal, 0, SC_PER_RHS * sizeof(double), c->stream));
-    LQ_CUDA(cudaMemsetAsync(tick, 0, sizeof(unsigned), c->stream));
+    LQ_CUDA(cudaMemsetAsync(tick, 0, 64 * sizeof(unsigned), c->stream));
     LQ_TRY(blas_norm2(c, B, P64, 1, rb64, 2, SC_TMP + 0));
     LQ_TRY(blas_zero(c, X, P64, 1, rb64, 2));
     double h[SC_PER_RHS];
@@ -222,6 +235,9 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     const double bn2 = h[SC_TMP + 0];
     const int block = 256;
     const dim3 grid(gcr_grid(c, block));
+    // the elementwise update: one thread per (parity, float4 chunk, site), at most 8 blocks per SM
+    const long nupd = (12L * c->g.Vh + block - 1) / block;
+    const int gu = (int)(nupd < 8 * 152 ? nupd : 8 * 152);
     bool sap = !net && c->sap_on;
     if (sap) LQ_TRY(sap_check(c, c->sap_bs));
     int iters = 0, restarts = 0, fallback = 0;
@@ -232,7 +248,8 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
     std::vector<double> wn(K);                       // |w^_j|^2
     std::vector<double> hd(GCR_NDOT);
     auto launch_dots = [&](int k, const char* wk) -> lqcd_status {
-        gcr_dots_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, parts, tick, dots);
+        const dim3 gd(grid.x, (k + GCR_CH - 1) / GCR_CH + 1);
+        gcr_dots_kernel<<<gd, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, parts, tick + 1, dots);
         LQ_CUDA(cudaGetLastError());
         c->launches++;
         return read(dots, hd.data(), GCR_NDOT);
@@ -243,7 +260,7 @@ lqcd_status solve_fgcr(lqcd_ctx* c, lqcd_net* net, double* x, const double* b, d
         for (int j = 0; j < k; ++j) st.c[j] = make_float2((float)cj[j].real(), (float)cj[j].imag());
         st.a = make_float2((float)a.real(), (float)a.imag());
         st.update_r = update_r ? 1 : 0;
-        gcr_orth_update_kernel<<<grid, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, st, parts, tick, upd);
+        gcr_orth_update_kernel<<<gu, block, 0, c->stream>>>(c->g, Wb, fld, k, wk, R32, st, parts, tick, upd);
         LQ_CUDA(cudaGetLastError());
         c->launches++;
         return read(upd, out, 2);

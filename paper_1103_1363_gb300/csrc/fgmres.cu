@@ -40,7 +40,10 @@ lqcd_status net_apply_internal(lqcd_net* n, void* z, const void* r, size_t rb);
 
 namespace {
 
-enum { ARN_CHUNK = 24, ARN_NV = 2 * ARN_CHUNK + 1, ARN_MAXCH = 16, DEFL_MAX = 16 };
+// Dots with the basis in chunks of ARN_CHUNK vectors per blockIdx.y: a thread
+// loads at most ARN_CHUNK + 1 fields per site (short chains of loads, many
+// blocks), at the cost of |w|^2 formed once per chunk.
+enum { ARN_CHUNK = 4, ARN_NV = 2 * ARN_CHUNK + 1, ARN_MAXCH = 32, DEFL_MAX = 16 };
 constexpr double CYCLE_REDUCTION = 1e-5;
 
 int arn_grid(const lqcd_ctx* c, int block)
@@ -52,7 +55,7 @@ int arn_grid(const lqcd_ctx* c, int block)
 }  // namespace
 
 // Dot products of w with a chunk of basis vectors per blockIdx.y:
-// out[ch * ARN_NV + 2i, +1] = <V_{24 ch + i}, w>, out[ch * ARN_NV + 48] = |w|^2.
+// out[ch * ARN_NV + 2i, +1] = <V_{ARN_CHUNK ch + i}, w>, out[ch * ARN_NV + 2 ARN_CHUNK] = |w|^2.
 __global__ void arn_dots_kernel(Geom g, const char* V, size_t fld, int n, const char* w, double* partials,
                                 size_t part_stride, unsigned* tickets, double* out)
 {
