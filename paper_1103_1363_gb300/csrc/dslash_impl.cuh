@@ -734,13 +734,16 @@ __global__ void __launch_bounds__(STG_NIN * STG_MAXLXH, 2) dslash_staged_kernel(
 template <int PG, int PS, int RECON, bool DAG, int EPI>
 cudaError_t launch_staged_t(const DslashArgs& A, int nrhs, cudaStream_t s)
 {
-    static bool attr = false;  // the largest buffer (Lx/2 = 16) is allowed once per instantiation
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(dslash_staged_kernel<PG, PS, RECON, DAG, EPI>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)staged_smem_bytes(PS, STG_MAXLXH));
+    // the largest buffer (Lx/2 = 16) is allowed once per instantiation and device
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        e = cudaFuncSetAttribute(dslash_staged_kernel<PG, PS, RECON, DAG, EPI>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged_smem_bytes(PS, STG_MAXLXH));
         if (e != cudaSuccess) return e;
-        attr = true;
+        if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     const long tiles = (long)(A.g.L[1] / STG_TY) * (A.g.L[2] / STG_TZ) * (A.g.L[3] / STG_TT);
     if (tiles * nrhs > 0x7fffffffL) return cudaErrorInvalidConfiguration;
