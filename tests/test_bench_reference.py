@@ -41,3 +41,18 @@ def test_reference_arm_reports_the_threads_used():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert run_bench({"RANK": "1"}) == []
+
+
+def test_failing_side_leg_is_reported_in_place(capsys):
+    """A comparison leg that raises is reported as {"error": ...} in its
+    place (and on stderr) instead of costing the run its JSON line; a leg
+    that works returns its result unchanged."""
+    import bench
+
+    def broken():
+        raise RuntimeError("device busy")
+
+    out = bench.guarded("solve", broken)
+    assert out == {"error": "RuntimeError: device busy"}
+    assert "leg solve failed" in capsys.readouterr().err
+    assert bench.guarded("ok", lambda a, b: a + b, 2, 3) == 5
